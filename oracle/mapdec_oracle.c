@@ -1,0 +1,629 @@
+/*
+ * FP64 CPU oracle for the BSID MAP decoder (test infrastructure only).
+ *
+ * This file is the plain, slow reference against which the CUDA decoder is
+ * checked.  Only the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark may load it; the decoder library never does.  It shares no
+ * code, header, table or helper with the CUDA path.
+ *
+ * Everything follows the paper's Sec. II (Preliminaries) in its own order and
+ * notation, in double precision:
+ *   - receiver metric R(y|x): the lattice of eqs. (F), (F_lastrow) with its
+ *     initial conditions, plus a cap of I insertions per transmitted bit;
+ *   - gamma_i(m', m, D) = Pr{D_i = D} R(Y[n i + m' .. n(i+1) + m) | C(D)),
+ *     eq. (gamma), evaluated on the paper's own (i, m', D) grid;
+ *   - the forward recursion with per-index normalisation, eqs. (alpha),
+ *     (alpha_norm), (alpha_prenorm); the backward recursion eq. (beta),
+ *     normalised the same way;
+ *   - the APPs, eqs. (L), (lambda), (sigma), normalised over D per symbol;
+ *   - the frame log-likelihood  log P(Y) = sum_i log c_i + log alpha_N(rho-tau)
+ *     where c_i are the forward normalisers of eq. (alpha_norm).
+ *
+ * Readings taken where the paper is silent (each also used by the tests):
+ *   - insertions before a transmitted bit are capped at I; weights are not
+ *     renormalised, so truncated paths are simply dropped;
+ *   - lattice rows/columns are 1-based: row r has consumed r bits, column j
+ *     has consumed j received bits; the diagonal into (r, j) compares x_r, y_j;
+ *   - each inserted bit has weight Pi/2 (uniform value, never substituted);
+ *   - an isolated frame with known length: alpha_0 = [m = 0],
+ *     beta_N = [m = rho - tau];
+ *   - drift limits: m in [-xmax, xmax] at symbol boundaries, drift change
+ *     m - m' in [-n, n I]; a window that starts before 0 or runs past rho
+ *     contributes nothing;
+ *   - beta is normalised by its own sum; APPs are normalised over D.
+ *
+ * Gradients (not in the paper): d logP / d(Pi, Pd, Ps) with Pt = 1 - Pi - Pd,
+ * by forward-mode dual numbers carried through every step above; and
+ * d logP / d Pr{D_i = D}, which follows from P(Y) being linear in each prior:
+ * P(Y) = sum_D Pr{D_i = D} Q_i(D), Q_i(D) = sum_{m',m} alpha_i(m') R beta_{i+1}(m).
+ *
+ * The optional memo caches R(.|C(D)) per (rx start p, D): the same lattice
+ * function evaluated once per key, so results are bitwise identical to the
+ * un-memoised (i, m', D) grid; it only saves time on large frames.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_DRIFT_RANGE 2
+#define ORC_ERR_ZERO_PROB 3
+#define ORC_ERR_NOMEM 4
+
+/* ------------------------------------------------------------------ */
+/* Receiver metric lattice, eqs. (F), (F_lastrow), with insertion cap I */
+/* ------------------------------------------------------------------ */
+
+/*
+ * x[0..n): transmitted bits x_1..x_n; y[0..mu): received bits y_1..y_mu.
+ * Writes out[j] = F_{n,j}, j = 0..mu: the probability that x is received as
+ * exactly y_1..y_j (eq. F_lastrow gives the last row).  The horizontal
+ * (insertion, weight Pi/2) steps of eq. (F) happen in rows r < n only, at
+ * most I of them in each row.  The corridor of Sec. II-C keeps only nodes
+ * with j - r in [m_n^-, m_n^+] = [-n, n I].
+ */
+int orc_receiver_metric(int n, int I, const uint8_t *x, const uint8_t *y, int mu,
+                        double Pi, double Pd, double Ps, double *out)
+{
+    if (n < 1 || I < 0 || mu < 0 || !x || (mu > 0 && !y) || !out) return ORC_ERR_ARG;
+    const double Pt = 1.0 - Pi - Pd;
+    const double half_pi = 0.5 * Pi;
+    double *F = (double *)calloc((size_t)(mu + 1), sizeof(double));
+    double *G = (double *)calloc((size_t)(mu + 1), sizeof(double));
+    double *wp = (double *)calloc((size_t)(I + 1), sizeof(double));
+    if (!F || !G || !wp) { free(F); free(G); free(wp); return ORC_ERR_NOMEM; }
+    wp[0] = 1.0;
+    for (int a = 1; a <= I; ++a) wp[a] = wp[a - 1] * half_pi;
+
+    /* initial condition: F_{0,0} = 1, everything else 0 */
+    F[0] = 1.0;
+    for (int r = 0; r < n; ++r) {
+        /* row r including its horizontal steps:
+           G_{r,j} = sum_{a=0}^{min(I,j)} (Pi/2)^a F_{r,j-a}              */
+        for (int j = 0; j <= mu; ++j) {
+            double g = 0.0;
+            for (int a = 0; a <= I && a <= j; ++a) g += wp[a] * F[j - a];
+            if (j - r < -n || j - r > n * I) g = 0.0; /* corridor */
+            G[j] = g;
+        }
+        /* row r+1 by vertical (deletion) and diagonal (transmission) steps:
+           F_{r+1,j} = Pd G_{r,j} + Qdot(y_j | x_{r+1}) G_{r,j-1}             */
+        for (int j = 0; j <= mu; ++j) {
+            double f = Pd * G[j];
+            if (j >= 1) {
+                const double Q = (y[j - 1] != x[r]) ? Pt * Ps : Pt * (1.0 - Ps);
+                f += Q * G[j - 1];
+            }
+            if (j - (r + 1) < -n || j - (r + 1) > n * I) f = 0.0; /* corridor */
+            F[j] = f;
+        }
+    }
+    memcpy(out, F, (size_t)(mu + 1) * sizeof(double));
+    free(F); free(G); free(wp);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Dual numbers for forward-mode derivatives w.r.t. (Pi, Pd, Ps)       */
+/* ------------------------------------------------------------------ */
+
+typedef struct { double v, d[3]; } dual;
+
+static inline dual d_const(double v) { dual r = {v, {0, 0, 0}}; return r; }
+static inline dual d_add(dual a, dual b)
+{
+    dual r = {a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}};
+    return r;
+}
+static inline dual d_mul(dual a, dual b)
+{
+    dual r;
+    r.v = a.v * b.v;
+    for (int k = 0; k < 3; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+static inline dual d_scale(dual a, double s)
+{
+    dual r = {a.v * s, {a.d[0] * s, a.d[1] * s, a.d[2] * s}};
+    return r;
+}
+static inline dual d_div(dual a, dual b)
+{
+    dual r;
+    r.v = a.v / b.v;
+    for (int k = 0; k < 3; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    return r;
+}
+static inline dual d_log(dual a)
+{
+    dual r;
+    r.v = log(a.v);
+    for (int k = 0; k < 3; ++k) r.d[k] = a.d[k] / a.v;
+    return r;
+}
+
+/* The same lattice as orc_receiver_metric, carried in dual numbers. */
+static int orc_receiver_metric_dual(int n, int I, const uint8_t *x, const uint8_t *y, int mu,
+                                    double Pi, double Pd, double Ps, dual *out)
+{
+    dual dPi = {Pi, {1, 0, 0}};
+    dual dPd = {Pd, {0, 1, 0}};
+    dual dPs = {Ps, {0, 0, 1}};
+    dual dPt = d_add(d_const(1.0), d_add(d_scale(dPi, -1.0), d_scale(dPd, -1.0)));
+    dual Qdiff = d_mul(dPt, dPs);
+    dual Qsame = d_mul(dPt, d_add(d_const(1.0), d_scale(dPs, -1.0)));
+    dual half_pi = d_scale(dPi, 0.5);
+    dual *F = (dual *)calloc((size_t)(mu + 1), sizeof(dual));
+    dual *G = (dual *)calloc((size_t)(mu + 1), sizeof(dual));
+    dual *wp = (dual *)calloc((size_t)(I + 1), sizeof(dual));
+    if (!F || !G || !wp) { free(F); free(G); free(wp); return ORC_ERR_NOMEM; }
+    wp[0] = d_const(1.0);
+    for (int a = 1; a <= I; ++a) wp[a] = d_mul(wp[a - 1], half_pi);
+    F[0] = d_const(1.0);
+    for (int r = 0; r < n; ++r) {
+        for (int j = 0; j <= mu; ++j) {
+            dual g = d_const(0.0);
+            for (int a = 0; a <= I && a <= j; ++a) g = d_add(g, d_mul(wp[a], F[j - a]));
+            if (j - r < -n || j - r > n * I) g = d_const(0.0);
+            G[j] = g;
+        }
+        for (int j = 0; j <= mu; ++j) {
+            dual f = d_mul(dPd, G[j]);
+            if (j >= 1) {
+                const dual Q = (y[j - 1] != x[r]) ? Qdiff : Qsame;
+                f = d_add(f, d_mul(Q, G[j - 1]));
+            }
+            if (j - (r + 1) < -n || j - (r + 1) > n * I) f = d_const(0.0);
+            F[j] = f;
+        }
+    }
+    memcpy(out, F, (size_t)(mu + 1) * sizeof(dual));
+    free(F); free(G); free(wp);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Frame context                                                       */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int q, n, N, I, xmax, M, Mn;
+    int64_t rho;
+    double Pi, Pd, Ps;
+    const uint8_t *cb;  /* q*n codeword bits */
+    const uint8_t *rx;  /* rho received bits */
+    const double *pri;  /* N*q priors, or NULL for uniform 1/q */
+    int memo;
+    double *Rm;         /* memo, (rho+1)*q*Mn, valid where Rk[p] set */
+    uint8_t *Rk;
+    dual *Rd;           /* dual memo for gradients */
+    uint8_t *Rdk;
+} orc_ctx;
+
+static double orc_prior(const orc_ctx *c, int i, int D)
+{
+    return c->pri ? c->pri[(size_t)i * c->q + D] : 1.0 / (double)c->q;
+}
+
+/* R(Y[p .. p+j) | C(D)) for j = 0..Mn-1 (entries with p + j > rho are 0). */
+static int orc_R(orc_ctx *c, int64_t p, int D, double *Rj)
+{
+    const int Mn = c->Mn;
+    if (c->memo && c->Rk[p]) {
+        memcpy(Rj, c->Rm + ((size_t)p * c->q + D) * Mn, (size_t)Mn * sizeof(double));
+        return ORC_OK;
+    }
+    int64_t avail = c->rho - p;
+    int mu = (int)(avail < (int64_t)(Mn - 1) ? avail : (int64_t)(Mn - 1));
+    for (int j = 0; j < Mn; ++j) Rj[j] = 0.0;
+    int st = orc_receiver_metric(c->n, c->I, c->cb + (size_t)D * c->n, c->rx + p, mu,
+                                 c->Pi, c->Pd, c->Ps, Rj);
+    if (st) return st;
+    if (c->memo) {
+        memcpy(c->Rm + ((size_t)p * c->q + D) * Mn, Rj, (size_t)Mn * sizeof(double));
+        if (D == c->q - 1) c->Rk[p] = 1;
+    }
+    return ORC_OK;
+}
+
+static int orc_R_dual(orc_ctx *c, int64_t p, int D, dual *Rj)
+{
+    const int Mn = c->Mn;
+    if (c->memo && c->Rdk[p]) {
+        memcpy(Rj, c->Rd + ((size_t)p * c->q + D) * Mn, (size_t)Mn * sizeof(dual));
+        return ORC_OK;
+    }
+    int64_t avail = c->rho - p;
+    int mu = (int)(avail < (int64_t)(Mn - 1) ? avail : (int64_t)(Mn - 1));
+    for (int j = 0; j < Mn; ++j) Rj[j] = d_const(0.0);
+    int st = orc_receiver_metric_dual(c->n, c->I, c->cb + (size_t)D * c->n, c->rx + p, mu,
+                                      c->Pi, c->Pd, c->Ps, Rj);
+    if (st) return st;
+    if (c->memo) {
+        memcpy(c->Rd + ((size_t)p * c->q + D) * Mn, Rj, (size_t)Mn * sizeof(dual));
+        if (D == c->q - 1) c->Rdk[p] = 1;
+    }
+    return ORC_OK;
+}
+
+/*
+ * gamma_i(m', m, D), eq. (gamma), for all m' in [-xmax, xmax], D, and
+ * drift change delta = m - m' in [-n, nI]; stored as
+ * g[((m'+xmax) * q + D) * Mn + (delta + n)].  Zero where m is outside the
+ * drift limits or the received window leaves [0, rho).
+ * If R is non-NULL the receiver metric without the prior is stored alongside.
+ */
+static int orc_gamma(orc_ctx *c, int i, double *g, double *R)
+{
+    const int M = c->M, q = c->q, n = c->n, Mn = c->Mn, xmax = c->xmax;
+    double *Rj = (double *)malloc((size_t)Mn * sizeof(double));
+    if (!Rj) return ORC_ERR_NOMEM;
+    for (int mp = 0; mp < M; ++mp) {
+        const int m1 = mp - xmax;
+        const int64_t p = (int64_t)n * i + m1;
+        for (int D = 0; D < q; ++D) {
+            double *gd = g + ((size_t)mp * q + D) * Mn;
+            double *Rd = R ? R + ((size_t)mp * q + D) * Mn : NULL;
+            if (p < 0 || p > c->rho) {
+                for (int k = 0; k < Mn; ++k) { gd[k] = 0.0; if (Rd) Rd[k] = 0.0; }
+                continue;
+            }
+            int st = orc_R(c, p, D, Rj);
+            if (st) { free(Rj); return st; }
+            const double pr = orc_prior(c, i, D);
+            for (int k = 0; k < Mn; ++k) {
+                const int m2 = m1 + (k - n);
+                const int inside = (m2 >= -xmax && m2 <= xmax);
+                gd[k] = inside ? pr * Rj[k] : 0.0;
+                if (Rd) Rd[k] = inside ? Rj[k] : 0.0;
+            }
+        }
+    }
+    free(Rj);
+    return ORC_OK;
+}
+
+static int orc_gamma_dual(orc_ctx *c, int i, dual *g)
+{
+    const int M = c->M, q = c->q, n = c->n, Mn = c->Mn, xmax = c->xmax;
+    dual *Rj = (dual *)malloc((size_t)Mn * sizeof(dual));
+    if (!Rj) return ORC_ERR_NOMEM;
+    for (int mp = 0; mp < M; ++mp) {
+        const int m1 = mp - xmax;
+        const int64_t p = (int64_t)n * i + m1;
+        for (int D = 0; D < q; ++D) {
+            dual *gd = g + ((size_t)mp * q + D) * Mn;
+            if (p < 0 || p > c->rho) {
+                for (int k = 0; k < Mn; ++k) gd[k] = d_const(0.0);
+                continue;
+            }
+            int st = orc_R_dual(c, p, D, Rj);
+            if (st) { free(Rj); return st; }
+            const double pr = orc_prior(c, i, D);
+            for (int k = 0; k < Mn; ++k) {
+                const int m2 = m1 + (k - n);
+                gd[k] = (m2 >= -xmax && m2 <= xmax) ? d_scale(Rj[k], pr) : d_const(0.0);
+            }
+        }
+    }
+    free(Rj);
+    return ORC_OK;
+}
+
+static int orc_init(orc_ctx *c, int q, int n, const uint8_t *codebook, int N, double Pi,
+                    double Pd, double Ps, int I, int xmax, const uint8_t *rx, int64_t rho,
+                    const double *priors, int memo, int want_dual)
+{
+    memset(c, 0, sizeof(*c));
+    if (q < 2 || n < 1 || n > 62 || N < 1 || I < 1 || xmax < 0 || !codebook || rho < 0 ||
+        (rho > 0 && !rx))
+        return ORC_ERR_ARG;
+    if (n < 31 && q > (1 << n)) return ORC_ERR_ARG;
+    if (!(Pi >= 0 && Pd >= 0 && Ps >= 0 && Ps <= 1 && Pi + Pd < 1)) return ORC_ERR_ARG;
+    int64_t tau = (int64_t)n * N;
+    if (rho - tau > xmax || tau - rho > xmax) return ORC_ERR_DRIFT_RANGE;
+    c->q = q; c->n = n; c->N = N; c->I = I; c->xmax = xmax;
+    c->M = 2 * xmax + 1; c->Mn = n * (I + 1) + 1;
+    c->rho = rho; c->Pi = Pi; c->Pd = Pd; c->Ps = Ps;
+    c->cb = codebook; c->rx = rx; c->pri = priors; c->memo = memo;
+    if (memo) {
+        size_t cells = (size_t)(rho + 1) * q * c->Mn;
+        if (want_dual) {
+            c->Rd = (dual *)malloc(cells * sizeof(dual));
+            c->Rdk = (uint8_t *)calloc((size_t)(rho + 1), 1);
+            if (!c->Rd || !c->Rdk) return ORC_ERR_NOMEM;
+        }
+        c->Rm = (double *)malloc(cells * sizeof(double));
+        c->Rk = (uint8_t *)calloc((size_t)(rho + 1), 1);
+        if (!c->Rm || !c->Rk) return ORC_ERR_NOMEM;
+    }
+    return ORC_OK;
+}
+
+static void orc_free(orc_ctx *c)
+{
+    free(c->Rm); free(c->Rk); free(c->Rd); free(c->Rdk);
+    c->Rm = NULL; c->Rk = NULL; c->Rd = NULL; c->Rdk = NULL;
+}
+
+/*
+ * Forward pass, eqs. (alpha_prenorm), (alpha_norm):
+ *   alpha'_{i+1}(m) = sum_{m', D} alpha_i(m') gamma_i(m', m, D),
+ *   c_{i+1} = sum_m alpha'_{i+1}(m),  alpha_{i+1} = alpha'_{i+1} / c_{i+1}.
+ * alpha rows (N+1)*M are written to A; returns sum_i log c_i in *logsum.
+ */
+static int orc_forward(orc_ctx *c, double *A, double *logsum)
+{
+    const int M = c->M, q = c->q, Mn = c->Mn, n = c->n;
+    double *g = (double *)malloc((size_t)M * q * Mn * sizeof(double));
+    if (!g) return ORC_ERR_NOMEM;
+    for (int m = 0; m < M; ++m) A[m] = 0.0;
+    A[c->xmax] = 1.0; /* alpha_0(m) = [m = 0] */
+    double ls = 0.0;
+    for (int i = 0; i < c->N; ++i) {
+        int st = orc_gamma(c, i, g, NULL);
+        if (st) { free(g); return st; }
+        const double *a = A + (size_t)i * M;
+        double *an = A + (size_t)(i + 1) * M;
+        for (int m = 0; m < M; ++m) an[m] = 0.0;
+        for (int mp = 0; mp < M; ++mp)
+            for (int D = 0; D < q; ++D) {
+                const double *gd = g + ((size_t)mp * q + D) * Mn;
+                for (int k = 0; k < Mn; ++k) {
+                    const int m = mp + k - n;
+                    if (m >= 0 && m < M) an[m] += a[mp] * gd[k];
+                }
+            }
+        double cs = 0.0;
+        for (int m = 0; m < M; ++m) cs += an[m];
+        if (!(cs > 0.0)) { free(g); return ORC_ERR_ZERO_PROB; }
+        for (int m = 0; m < M; ++m) an[m] /= cs;
+        ls += log(cs);
+    }
+    free(g);
+    *logsum = ls;
+    return ORC_OK;
+}
+
+/*
+ * Backward pass, eq. (beta):
+ *   beta_i(m) = sum_{m', D} beta_{i+1}(m') gamma_i(m, m', D),
+ * normalised by its own sum; beta_N(m) = [m = rho - tau].
+ */
+static int orc_backward(orc_ctx *c, double *B)
+{
+    const int M = c->M, q = c->q, Mn = c->Mn, n = c->n, N = c->N;
+    double *g = (double *)malloc((size_t)M * q * Mn * sizeof(double));
+    if (!g) return ORC_ERR_NOMEM;
+    double *bN = B + (size_t)N * M;
+    for (int m = 0; m < M; ++m) bN[m] = 0.0;
+    bN[(int)(c->rho - (int64_t)n * N) + c->xmax] = 1.0;
+    for (int i = N - 1; i >= 0; --i) {
+        int st = orc_gamma(c, i, g, NULL);
+        if (st) { free(g); return st; }
+        const double *bn = B + (size_t)(i + 1) * M;
+        double *b = B + (size_t)i * M;
+        for (int m = 0; m < M; ++m) {
+            double s = 0.0;
+            for (int D = 0; D < q; ++D) {
+                const double *gd = g + ((size_t)m * q + D) * Mn;
+                for (int k = 0; k < Mn; ++k) {
+                    const int m2 = m + k - n;
+                    if (m2 >= 0 && m2 < M) s += bn[m2] * gd[k];
+                }
+            }
+            b[m] = s;
+        }
+        double ds = 0.0;
+        for (int m = 0; m < M; ++m) ds += b[m];
+        if (!(ds > 0.0)) { free(g); return ORC_ERR_ZERO_PROB; }
+        for (int m = 0; m < M; ++m) b[m] /= ds;
+    }
+    free(g);
+    return ORC_OK;
+}
+
+/*
+ * APPs, eqs. (L), (sigma): L_i(D) proportional to
+ *   sum_{m', m} alpha_i(m') gamma_i(m', m, D) beta_{i+1}(m),
+ * normalised over D.  If Qout is given, also writes
+ *   Q_i(D) = sum_{m', m} alpha_i(m') R beta_{i+1}(m)   (gamma without prior)
+ * and Z_i = sum_D Pr{D_i=D} Q_i(D) to Zout.
+ */
+static int orc_app(orc_ctx *c, const double *A, const double *B, double *app, double *Qout,
+                   double *Zout)
+{
+    const int M = c->M, q = c->q, Mn = c->Mn, n = c->n, N = c->N;
+    double *g = (double *)malloc((size_t)M * q * Mn * sizeof(double));
+    double *R = Qout ? (double *)malloc((size_t)M * q * Mn * sizeof(double)) : NULL;
+    double *L = (double *)malloc((size_t)q * sizeof(double));
+    if (!g || !L || (Qout && !R)) { free(g); free(R); free(L); return ORC_ERR_NOMEM; }
+    for (int i = 0; i < N; ++i) {
+        int st = orc_gamma(c, i, g, R);
+        if (st) { free(g); free(R); free(L); return st; }
+        const double *a = A + (size_t)i * M;
+        const double *bn = B + (size_t)(i + 1) * M;
+        double tot = 0.0;
+        for (int D = 0; D < q; ++D) {
+            double s = 0.0, sq = 0.0;
+            for (int mp = 0; mp < M; ++mp) {
+                const double *gd = g + ((size_t)mp * q + D) * Mn;
+                const double *Rd = R ? R + ((size_t)mp * q + D) * Mn : NULL;
+                for (int k = 0; k < Mn; ++k) {
+                    const int m = mp + k - n;
+                    if (m >= 0 && m < M) {
+                        s += a[mp] * gd[k] * bn[m];
+                        if (Rd) sq += a[mp] * Rd[k] * bn[m];
+                    }
+                }
+            }
+            L[D] = s;
+            tot += s;
+            if (Qout) Qout[(size_t)i * q + D] = sq;
+        }
+        if (!(tot > 0.0)) { free(g); free(R); free(L); return ORC_ERR_ZERO_PROB; }
+        if (app)
+            for (int D = 0; D < q; ++D) app[(size_t)i * q + D] = L[D] / tot;
+        if (Zout) Zout[i] = tot;
+    }
+    free(g); free(R); free(L);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Public entry points                                                 */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Full decode of one frame: APPs (N*q, row i sums to 1) and log P(Y).
+ * priors: N*q, row i = Pr{D_i = .}; NULL means uniform 1/q.
+ */
+int orc_decode(int q, int n, const uint8_t *codebook, int N, double Pi, double Pd, double Ps,
+               int I, int xmax, const uint8_t *rx, int64_t rho, const double *priors, int memo,
+               double *app, double *loglik)
+{
+    orc_ctx c;
+    int st = orc_init(&c, q, n, codebook, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, memo, 0);
+    if (st) { orc_free(&c); return st; }
+    const size_t rows = (size_t)(N + 1) * c.M;
+    double *A = (double *)malloc(rows * sizeof(double));
+    double *B = (double *)malloc(rows * sizeof(double));
+    if (!A || !B) { free(A); free(B); orc_free(&c); return ORC_ERR_NOMEM; }
+    double ls = 0.0;
+    st = orc_forward(&c, A, &ls);
+    if (!st) {
+        const double aN = A[(size_t)N * c.M + (int)(rho - (int64_t)n * N) + xmax];
+        if (!(aN > 0.0)) st = ORC_ERR_ZERO_PROB;
+        else if (loglik) *loglik = ls + log(aN);
+    }
+    if (!st && app) st = orc_backward(&c, B);
+    if (!st && app) st = orc_app(&c, A, B, app, NULL, NULL);
+    free(A); free(B); orc_free(&c);
+    return st;
+}
+
+/*
+ * Normalised forward/backward metrics and forward normalisers, for tests of
+ * the invariants.  A, B: (N+1)*M each; logc: N entries (log c_1..log c_N).
+ */
+int orc_forward_backward(int q, int n, const uint8_t *codebook, int N, double Pi, double Pd,
+                         double Ps, int I, int xmax, const uint8_t *rx, int64_t rho,
+                         const double *priors, double *A, double *B, double *logc)
+{
+    orc_ctx c;
+    int st = orc_init(&c, q, n, codebook, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, 1, 0);
+    if (st) { orc_free(&c); return st; }
+    double ls = 0.0;
+    st = orc_forward(&c, A, &ls);
+    if (!st && logc) {
+        /* recover each log c_i by re-running the normaliser sums */
+        const int M = c.M;
+        double *g = (double *)malloc((size_t)M * q * c.Mn * sizeof(double));
+        double *an = (double *)malloc((size_t)M * sizeof(double));
+        if (!g || !an) st = ORC_ERR_NOMEM;
+        for (int i = 0; !st && i < N; ++i) {
+            st = orc_gamma(&c, i, g, NULL);
+            if (st) break;
+            for (int m = 0; m < M; ++m) an[m] = 0.0;
+            for (int mp = 0; mp < M; ++mp)
+                for (int D = 0; D < q; ++D) {
+                    const double *gd = g + ((size_t)mp * q + D) * c.Mn;
+                    for (int k = 0; k < c.Mn; ++k) {
+                        const int m = mp + k - n;
+                        if (m >= 0 && m < M) an[m] += A[(size_t)i * M + mp] * gd[k];
+                    }
+                }
+            double cs = 0.0;
+            for (int m = 0; m < M; ++m) cs += an[m];
+            logc[i] = log(cs);
+        }
+        free(g); free(an);
+    }
+    if (!st) st = orc_backward(&c, B);
+    orc_free(&c);
+    return st;
+}
+
+/*
+ * log P(Y) and its gradient:
+ *   dlogp_dchan[0..2] = d logP / d(Pi, Pd, Ps) with Pt = 1 - Pi - Pd and the
+ *   drift limits held fixed (forward-mode dual numbers through the lattice
+ *   and the forward pass);
+ *   dlogp_dpriors[i*q + D] = d logP / d Pr{D_i = D} = Q_i(D) / Z_i.
+ * Either output may be NULL.
+ */
+int orc_loglik_grad(int q, int n, const uint8_t *codebook, int N, double Pi, double Pd,
+                    double Ps, int I, int xmax, const uint8_t *rx, int64_t rho,
+                    const double *priors, int memo, double *dlogp_dchan, double *dlogp_dpriors,
+                    double *loglik)
+{
+    orc_ctx c;
+    int st = orc_init(&c, q, n, codebook, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, memo,
+                      dlogp_dchan != NULL);
+    if (st) { orc_free(&c); return st; }
+    const int M = c.M, Mn = c.Mn;
+    const int end = (int)(rho - (int64_t)n * N) + xmax;
+    if (dlogp_dchan) {
+        dual *g = (dual *)malloc((size_t)M * q * Mn * sizeof(dual));
+        dual *a = (dual *)malloc((size_t)M * sizeof(dual));
+        dual *an = (dual *)malloc((size_t)M * sizeof(dual));
+        if (!g || !a || !an) st = ORC_ERR_NOMEM;
+        dual ls = d_const(0.0);
+        if (!st) {
+            for (int m = 0; m < M; ++m) a[m] = d_const(0.0);
+            a[xmax] = d_const(1.0);
+        }
+        for (int i = 0; !st && i < N; ++i) {
+            st = orc_gamma_dual(&c, i, g);
+            if (st) break;
+            for (int m = 0; m < M; ++m) an[m] = d_const(0.0);
+            for (int mp = 0; mp < M; ++mp)
+                for (int D = 0; D < q; ++D) {
+                    const dual *gd = g + ((size_t)mp * q + D) * Mn;
+                    for (int k = 0; k < Mn; ++k) {
+                        const int m = mp + k - n;
+                        if (m >= 0 && m < M) an[m] = d_add(an[m], d_mul(a[mp], gd[k]));
+                    }
+                }
+            dual cs = d_const(0.0);
+            for (int m = 0; m < M; ++m) cs = d_add(cs, an[m]);
+            if (!(cs.v > 0.0)) { st = ORC_ERR_ZERO_PROB; break; }
+            for (int m = 0; m < M; ++m) a[m] = d_div(an[m], cs);
+            ls = d_add(ls, d_log(cs));
+        }
+        if (!st) {
+            if (!(a[end].v > 0.0)) st = ORC_ERR_ZERO_PROB;
+            else {
+                dual lp = d_add(ls, d_log(a[end]));
+                for (int k = 0; k < 3; ++k) dlogp_dchan[k] = lp.d[k];
+                if (loglik) *loglik = lp.v;
+            }
+        }
+        free(g); free(a); free(an);
+        if (st) { orc_free(&c); return st; }
+    }
+    if (dlogp_dpriors || (!dlogp_dchan && loglik)) {
+        const size_t rows = (size_t)(N + 1) * M;
+        double *A = (double *)malloc(rows * sizeof(double));
+        double *B = (double *)malloc(rows * sizeof(double));
+        double *Z = (double *)malloc((size_t)N * sizeof(double));
+        if (!A || !B || !Z) st = ORC_ERR_NOMEM;
+        double ls = 0.0;
+        if (!st) st = orc_forward(&c, A, &ls);
+        if (!st && !dlogp_dchan && loglik) {
+            const double aN = A[(size_t)N * M + end];
+            if (!(aN > 0.0)) st = ORC_ERR_ZERO_PROB;
+            else *loglik = ls + log(aN);
+        }
+        if (!st && dlogp_dpriors) st = orc_backward(&c, B);
+        if (!st && dlogp_dpriors) st = orc_app(&c, A, B, NULL, dlogp_dpriors, Z);
+        if (!st && dlogp_dpriors)
+            for (int i = 0; i < N; ++i)
+                for (int D = 0; D < q; ++D) dlogp_dpriors[(size_t)i * q + D] /= Z[i];
+        free(A); free(B); free(Z);
+    }
+    orc_free(&c);
+    return st;
+}
