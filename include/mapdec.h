@@ -1,0 +1,218 @@
+/*
+ * mapdec.h -- C ABI of libmapdec.so, a GB300 (sm_103a) MAP decoder for the
+ * Davey-MacKay binary substitution/insertion/deletion (BSID) channel.
+ *
+ * The decoder computes, for a frame of N q-ary symbols each sent as an n-bit
+ * codeword C(D) and received as rho bits Y through the BSID channel
+ * (Briffa, "GPU Implementation and Optimization of a Flexible MAP Decoder for
+ * Synchronization Correction", Sec. II):
+ *   (1) the receiver metric R(Y[p .. p+j) | C(D)) for every start p, codeword D
+ *       and received length j, by the lattice of eqs. (F), (F_lastrow) with at
+ *       most I insertions before each transmitted bit;
+ *   (2) gamma_i(m', m, D) = Pr{D_i = D} R(...) (eq. gamma) and the forward and
+ *       backward recursions of eqs. (alpha), (beta) with per-index
+ *       normalisation (eqs. alpha_norm, alpha_prenorm);
+ *   (3) the a-posteriori probabilities L_i(D) of eqs. (L), (lambda), (sigma),
+ *       normalised over D for every symbol;
+ *   (4) the frame log-likelihood log P(Y) = sum_i log c_i + log alpha_N(rho-tau),
+ *       c_i the forward normalisers of eq. (alpha_norm).
+ * Gradients of log P(Y) (not in the paper) are provided by an adjoint path.
+ *
+ * Conventions shared by every entry point
+ *   - Drift states m lie in [-xmax, xmax] at symbol boundaries; the drift
+ *     change over one symbol lies in [-n, n*I].  The frame is isolated and its
+ *     received length rho is known: alpha_0 = [m = 0], beta_N = [m = rho - tau],
+ *     tau = n*N.  |rho - tau| must not exceed xmax.
+ *   - Bits are passed one per byte (0 or 1).  A codebook is q*n bytes,
+ *     row D = C(D) = (x_1 .. x_n); rows must be distinct (the encoding is
+ *     injective, Sec. II-A).
+ *   - Priors are N*q floats, row i = Pr{D_i = .}, entries >= 0, each row with a
+ *     positive sum; they are used as given (not renormalised).  NULL means
+ *     uniform 1/q.
+ *   - Arithmetic: FP32 for the lattice, gamma, alpha, beta and APPs; FP64 for
+ *     the sum of log normalisers and for gradient reductions.
+ *   - Every data pointer may be host or device memory (detected per call).
+ *     The caller owns all buffers; a handle owns its device scratch.
+ *     Work is issued on the handle's stream.  mapdec_decode,
+ *     mapdec_loglik_grad, mapdec_receiver_metric, mapdec_batch_decode and
+ *     mapdec_batch_loglik_grad return after that stream has drained, so
+ *     their status covers the whole computation; mapdec_batch_run is
+ *     asynchronous.
+ *   - There is no CPU fallback: if no CUDA device is usable the calls fail
+ *     with MAPDEC_ERR_CUDA.
+ *   - A handle must not be used from two threads at once.
+ *   - Every call returns a status; mapdec_strerror() names it.
+ */
+#ifndef MAPDEC_H
+#define MAPDEC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MAPDEC_OK = 0,
+    MAPDEC_ERR_ARG = 1,         /* invalid argument (sizes, probabilities, codebook) */
+    MAPDEC_ERR_DRIFT_RANGE = 2, /* |rho - tau| > xmax */
+    MAPDEC_ERR_ZERO_PROB = 3,   /* no channel path within the drift limits explains Y */
+    MAPDEC_ERR_NOMEM = 4,       /* device or host allocation failed */
+    MAPDEC_ERR_CUDA = 5,        /* CUDA runtime error or no usable device */
+    MAPDEC_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    MAPDEC_ERR_UNSUPPORTED = 7  /* parameters outside what the kernels support */
+};
+
+typedef struct mapdec mapdec_t;
+
+/*
+ * Create a decoder for one code and channel (Sec. II-A, II-B).
+ *   q >= 2 codewords of n bits (1 <= n <= 31, q <= 2^n, n*(I+1) <= 63),
+ *   codebook: q*n bytes (host or device), distinct rows;
+ *   N >= 1 symbols per frame; channel Pi, Pd, Ps with Pi, Pd, Ps >= 0,
+ *   Pi + Pd < 1, Ps <= 1; insertion cap I >= 1; drift limit xmax >= 0.
+ * Allocates device scratch sized for the largest received length tau + xmax.
+ * On success *out holds the handle (destroy with mapdec_destroy).
+ */
+int mapdec_create(mapdec_t **out, int q, int n, const uint8_t *codebook, int N, double Pi,
+                  double Pd, double Ps, int I, int xmax);
+
+/* Issue all work of this handle on `cuda_stream` (a cudaStream_t; NULL = default stream). */
+int mapdec_set_stream(mapdec_t *h, void *cuda_stream);
+
+/*
+ * Decode one frame: steps (1)-(4) above.
+ *   rx: rx_len received bits (one per byte); priors: N*q floats or NULL;
+ *   app_out: N*q floats, row i = L_i(.), sums to 1;  loglik_out: 1 double.
+ * Either output may be NULL.  Returns MAPDEC_ERR_DRIFT_RANGE if
+ * |rx_len - n*N| > xmax, MAPDEC_ERR_ZERO_PROB if P(Y) = 0 within the limits.
+ * The call returns after the work has completed on the handle's stream (the
+ * status of the decode is known only then).
+ */
+int mapdec_decode(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *priors,
+                  float *app_out, double *loglik_out);
+
+/*
+ * log P(Y) and its gradient (the adjoint path; not in the paper):
+ *   dlogp_dchan[0..2] = d logP / d(Pi, Pd, Ps), with Pt = 1 - Pi - Pd and the
+ *     drift limits held fixed (FP64);
+ *   dlogp_dpriors: N*q floats, d logP / d Pr{D_i = D};
+ *   loglik_out: log P(Y).
+ * Requires Pd > 0 and Pt*(1-Ps) > 0.  Any output may be NULL.
+ */
+int mapdec_loglik_grad(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *priors,
+                       double *dlogp_dchan, float *dlogp_dpriors, double *loglik_out);
+
+/*
+ * Step (1) alone: R_out[(p*q + D)*(n*(I+1)+1) + j] = R(Y[p .. p+j) | C(D)) for
+ * p = 0..rx_len, D < q, j = 0..n*(I+1); entries with p + j > rx_len are 0.
+ * R_out holds (rx_len+1)*q*(n*(I+1)+1) floats.
+ */
+int mapdec_receiver_metric(mapdec_t *h, const uint8_t *rx, int64_t rx_len, float *R_out);
+
+/* Release a handle and its device scratch (NULL is ignored). */
+void mapdec_destroy(mapdec_t *h);
+
+/* Static string for a status code. */
+const char *mapdec_strerror(int status);
+
+/* ------------------------------------------------------------------------ */
+/* Batched decoding of many frames with different codes and channels         */
+/* ------------------------------------------------------------------------ */
+
+/* One frame of a batch: its code, channel, drift limit and received length. */
+typedef struct {
+    int q, n, N, I, xmax;
+    double Pi, Pd, Ps;
+    const uint8_t *codebook; /* q*n bytes, host or device; copied at create */
+    int64_t rx_len;          /* rho of this frame */
+} mapdec_frame_desc_t;
+
+/* batch flags */
+enum {
+    MAPDEC_BATCH_GRAPH = 1,  /* capture the launch sequence in a CUDA graph */
+    MAPDEC_BATCH_PLAIN = 2,  /* one frame per launch, default tile sizes, no graph */
+    MAPDEC_BATCH_GRAD = 4    /* allocate for mapdec_batch_loglik_grad */
+};
+
+typedef struct mapdec_batch mapdec_batch_t;
+
+/*
+ * Plan a batch: frames[0..num_frames).  Validates every frame (as
+ * mapdec_create plus |rx_len - n*N| <= xmax), chooses tile sizes (from the
+ * tuning table if one was loaded), allocates device scratch within
+ * `mem_budget_bytes` (0 = 60% of free device memory; frames are processed in
+ * waves that fit) and the batch's own device input/output buffers.
+ * Frame f's bits, priors and APPs sit in concatenated buffers at the offsets
+ * reported by mapdec_batch_layout.
+ */
+int mapdec_batch_create(mapdec_batch_t **out, const mapdec_frame_desc_t *frames, int num_frames,
+                        int flags, int64_t mem_budget_bytes);
+
+/*
+ * Offsets of frame f in the concatenated buffers (host arrays of num_frames):
+ * rx_offsets[f] (bytes), sym_offsets[f] (rows of q floats, i.e. priors and
+ * APPs of frame f start at element sym_offsets[f]).  Also the totals.
+ */
+int mapdec_batch_layout(mapdec_batch_t *b, int64_t *rx_offsets, int64_t *sym_offsets,
+                        int64_t *rx_total, int64_t *prior_elems_total);
+
+/*
+ * Device pointers of the batch's resident input/output buffers, so callers
+ * can fill inputs in place and run without copies (any may be NULL).
+ */
+int mapdec_batch_buffers(mapdec_batch_t *b, uint8_t **rx_dev, float **priors_dev,
+                         float **app_dev, double **loglik_dev);
+
+/*
+ * Byte offset of frame f's bits inside the resident rx buffer returned by
+ * mapdec_batch_buffers (frames are padded to 16 bytes there); -1 if f is out
+ * of range.  Priors and APPs use the sym_offsets of mapdec_batch_layout.
+ */
+int64_t mapdec_batch_rx_offset(mapdec_batch_t *b, int frame);
+
+/*
+ * Decode the resident inputs into the resident outputs.  Stream-ordered and
+ * asynchronous: call mapdec_batch_sync (or synchronise the stream) before
+ * reading the outputs.
+ */
+int mapdec_batch_run(mapdec_batch_t *b);
+
+/* Wait for the batch's stream; returns the worst per-frame status of the last run. */
+int mapdec_batch_sync(mapdec_batch_t *b);
+
+/* Per-frame status of the last run (host array of num_frames ints; synchronous). */
+int mapdec_batch_status(mapdec_batch_t *b, int *status_per_frame);
+
+/*
+ * Decode all frames: copies rx_all / priors_all (host or device; priors_all
+ * may be NULL = uniform) into the resident buffers, runs, and copies APPs and
+ * log-likelihoods to app_all / loglik_all (host or device, may be NULL).
+ */
+int mapdec_batch_decode(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
+                        float *app_all, double *loglik_all);
+
+/*
+ * Gradients for every frame (batch created with MAPDEC_BATCH_GRAD):
+ * dchan_all[3*f + k] = d logP_f / d(Pi, Pd, Ps)_k, dpriors_all like app_all.
+ */
+int mapdec_batch_loglik_grad(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
+                             double *dchan_all, float *dpriors_all, double *loglik_all);
+
+/* Issue the batch's work on `cuda_stream` (a cudaStream_t; NULL = default stream). */
+int mapdec_batch_set_stream(mapdec_batch_t *b, void *cuda_stream);
+
+/* Release a batch, its CUDA graph and all its device buffers (NULL is ignored). */
+void mapdec_batch_destroy(mapdec_batch_t *b);
+
+/*
+ * Number of kernel launches the last run issued (graph nodes count as
+ * launches).  For accounting in benchmarks.
+ */
+int64_t mapdec_batch_last_launches(mapdec_batch_t *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAPDEC_H */

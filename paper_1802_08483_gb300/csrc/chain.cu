@@ -1,0 +1,333 @@
+// Sequential parts of the decoder and small helper kernels.
+//
+//   k_pack     : received bits (one per byte) -> 32-bit words.
+//   k_chain    : the forward recursion (eqs. alpha_prenorm, alpha_norm) or the
+//                backward recursion (eq. beta, normalised by its sum) of one
+//                frame, one CTA per (frame, direction).  The per-symbol
+//                transition sums W_i(s', j) stream from global memory into
+//                shared memory by 1-D bulk copies (cp.async.bulk) completed on
+//                mbarriers, double-buffered, while the previous chunk is used.
+//                The forward chain accumulates sum_i log c_i in FP64 and writes
+//                log P(Y) = sum_i log c_i + log alpha_N(rho - tau).
+//   k_finalize : APPs (eq. L, normalised over D), d logP / d prior and the
+//                FP64 reduction of the channel-parameter gradient.
+#include "mapdec_dev.cuh"
+#include "mapdec_kernels.h"
+
+namespace mdk {
+
+// ---------------------------------------------------------------------------
+__global__ void k_pack(const FrameDev *__restrict__ frames, const uint8_t *const *rx_bytes,
+                       uint32_t *const *rx_words, int nframes) {
+    const int fi = blockIdx.y;
+    if (fi >= nframes) return;
+    const long long rho = frames[fi].rho;
+    const uint8_t *src = rx_bytes[fi];
+    uint32_t *dst = rx_words[fi];
+    const long long nwords = (rho + 31) / 32 + 3;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+         w += (long long)gridDim.x * blockDim.x) {
+        uint32_t v = 0;
+        const long long b0 = w * 32;
+        for (int b = 0; b < 32; ++b) {
+            const long long k = b0 + b;
+            if (k < rho && src[k]) v |= (1u << b);
+        }
+        dst[w] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+constexpr int kChainThreads = 256;
+constexpr int kStages = 2;
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += red[w];  // every thread, same order: same result
+    return s;
+}
+
+// Geometry of chunk k of the step that consumes W_i.
+struct ChunkGeom {
+    int d0, d1;     // owned states (alpha: destinations, beta: sources)
+    int r0, r1;     // W rows staged
+    int shift;      // floats between the aligned copy start and row r0
+    uint32_t bytes; // copy size
+    const float *src;
+};
+
+__device__ __forceinline__ ChunkGeom chunk_geom(const FrameDev &f, int dir, int i, int k) {
+    ChunkGeom g;
+    const int CD = f.chainCD, M = f.M;
+    g.d0 = k * CD;
+    g.d1 = min(M, g.d0 + CD);
+    if (dir == 0) {  // destination s gets sources s - nI .. s + n
+        g.r0 = max(0, g.d0 - f.n * f.I);
+        g.r1 = min(M, g.d1 + f.n);
+    } else {
+        g.r0 = g.d0;
+        g.r1 = g.d1;
+    }
+    const long long o0 = (long long)i * f.wblk + (long long)g.r0 * f.MNS;
+    const long long o1 = (long long)i * f.wblk + (long long)g.r1 * f.MNS;
+    const long long a0 = o0 & ~3ll;
+    const long long a1 = (o1 + 3) & ~3ll;
+    g.shift = (int)(o0 - a0);
+    g.bytes = (uint32_t)((a1 - a0) * 4);
+    if (g.bytes == 0) g.bytes = 16;
+    g.src = f.W + a0;
+    return g;
+}
+
+__global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restrict__ frames,
+                                                         const Work *__restrict__ work) {
+    const Work wk = work[blockIdx.x];
+    const FrameDev &f = frames[wk.frame];
+    const int dir = wk.tile;  // 0 = forward (alpha), 1 = backward (beta)
+    const int M = f.M, Mp = f.Mp, MNS = f.MNS, MN = f.MN, n = f.n, N = f.N, xmax = f.xmax;
+    const long long rho = f.rho;
+    const int CD = f.chainCD;
+    const int nck = (M + CD - 1) / CD;
+    const long long total = (long long)N * nck;
+    const int send = (int)(rho - (long long)n * N) + xmax;  // state of the end drift
+
+    __shared__ uint64_t bar[kStages];
+    __shared__ double red[32];
+    __shared__ int s_fail;
+    extern __shared__ float4 sm4[];
+    float *cur = reinterpret_cast<float *>(sm4);
+    float *nxt = cur + Mp;
+    float *stage0 = nxt + Mp;
+    const size_t stageFloats = ((size_t)(CD + MN + 1) * MNS + 8 + 3) & ~(size_t)3;
+
+    for (int s = threadIdx.x; s < Mp; s += blockDim.x) {
+        cur[s] = (s == (dir == 0 ? xmax : send)) ? 1.f : 0.f;
+        nxt[s] = 0.f;
+    }
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    {
+        float *row0 = (dir == 0) ? f.alpha : f.beta + (size_t)N * Mp;
+        for (int s = threadIdx.x; s < Mp; s += blockDim.x) row0[s] = cur[s];
+    }
+    auto step_symbol = [&](long long g) -> int {
+        const int st = (int)(g / nck);
+        return dir == 0 ? st : N - 1 - st;
+    };
+    auto issue = [&](long long g) {
+        const int i = step_symbol(g);
+        const int k = (int)(g % nck);
+        const ChunkGeom cg = chunk_geom(f, dir, i, k);
+        uint64_t *b = &bar[g % kStages];
+        float *dst = stage0 + (size_t)(g % kStages) * stageFloats;
+        mbar_expect_tx(b, cg.bytes);
+        bulk_g2s(dst, cg.src, cg.bytes, b);
+    };
+    if (threadIdx.x == 0)
+        for (long long g = 0; g < kStages && g < total; ++g) issue(g);
+
+    double logsum = 0.0;
+    double part = 0.0;  // this thread's share of the current normaliser
+    bool failed = false;
+    long long gfail = 0;
+    for (long long g = 0; g < total; ++g) {
+        const int i = step_symbol(g);
+        const int k = (int)(g % nck);
+        const ChunkGeom cg = chunk_geom(f, dir, i, k);
+        const float *buf = stage0 + (size_t)(g % kStages) * stageFloats + cg.shift;
+        if (!mbar_wait(&bar[g % kStages], (uint32_t)((g / kStages) & 1), kWaitLimit)) {
+            atomicExch(&s_fail, ST_TIMEOUT);
+        }
+        // valid source rows: window start p = n i + s - xmax inside [0, rho]
+        const int vlo = max(0, (int)max(0ll, (long long)xmax - (long long)n * i));
+        const long long vhi_l = rho - (long long)n * i + xmax;
+        const int vhi = (int)min((long long)M - 1, vhi_l);
+        if (dir == 0) {
+            const int lo = max(cg.r0, vlo), hi = min(cg.r1 - 1, vhi);
+            for (int s = cg.d0 + threadIdx.x; s < cg.d1; s += blockDim.x) {
+                float acc = 0.f;
+                const int jlo = max(0, s + n - hi), jhi = min(MN - 1, s + n - lo);
+                for (int j = jlo; j <= jhi; ++j) {
+                    const int src = s - j + n;
+                    acc = fmaf(cur[src], buf[(size_t)(src - cg.r0) * MNS + j], acc);
+                }
+                nxt[s] = acc;
+                part += (double)acc;
+            }
+        } else {
+            for (int s = cg.d0 + threadIdx.x; s < cg.d1; s += blockDim.x) {
+                float acc = 0.f;
+                if (s >= vlo && s <= vhi) {
+                    const int jlo = max(0, n - s), jhi = min(MN - 1, M - 1 - s + n);
+                    const float *w = buf + (size_t)(s - cg.r0) * MNS;
+                    for (int j = jlo; j <= jhi; ++j) acc = fmaf(w[j], cur[s + j - n], acc);
+                }
+                nxt[s] = acc;
+                part += (double)acc;
+            }
+        }
+        __syncthreads();  // stage consumed by everyone
+        if (threadIdx.x == 0 && g + kStages < total) issue(g + kStages);
+        if (k == nck - 1) {
+            // end of a step: normalise
+            const double c = block_sum(part, red);
+            part = 0.0;
+            if (!(c > 0.0) || !isfinite(c)) {
+                if (threadIdx.x == 0) atomicCAS(&s_fail, 0, ST_ZERO);
+            }
+            __syncthreads();
+            if (s_fail) { failed = true; gfail = g; break; }
+            const float inv = (float)(1.0 / c);
+            if (dir == 0) logsum += log(c);
+            float *row = (dir == 0) ? f.alpha + (size_t)(i + 1) * Mp : f.beta + (size_t)i * Mp;
+            for (int s = threadIdx.x; s < M; s += blockDim.x) {
+                const float v = nxt[s] * inv;
+                cur[s] = v;
+                row[s] = v;
+            }
+            __syncthreads();
+        }
+    }
+    if (failed) {
+        // Copies already issued (chunks g+1 .. g+kStages) must land before the
+        // CTA's shared memory is released: wait for them, again with a bound.
+        if (threadIdx.x == 0) {
+            for (long long h = gfail + 1; h <= gfail + kStages && h < total; ++h)
+                mbar_wait(&bar[h % kStages], (uint32_t)((h / kStages) & 1), kWaitLimit);
+            atomicMax(f.status, s_fail);
+        }
+        __syncthreads();
+        return;
+    }
+    if (dir == 0 && threadIdx.x == 0) {
+        const float aN = cur[send];
+        if (!(aN > 0.f)) {
+            atomicMax(f.status, ST_ZERO);
+        } else {
+            *f.loglik = logsum + log((double)aN);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One CTA per frame; one warp per symbol at a time, lanes over D.
+constexpr int kFinThreads = 256;
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__restrict__ frames,
+                                                          int grad) {
+    const FrameDev &f = frames[blockIdx.x];
+    __shared__ double red[3][32];
+    if (*f.status != ST_OK) return;
+    const int q = f.q, n = f.n, N = f.N, xmax = f.xmax;
+    const long long P2 = (long long)f.P * f.nsub;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const double Pt = f.dPt, Ps = f.dPs, Pd = f.dPd;
+    const double Qm = Pt * (1.0 - Ps), Qs = Pt * Ps;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    bool bad = false;
+    for (int i = warp; i < N; i += nw) {
+        long long plo = (long long)n * i - xmax, phi = (long long)n * i + xmax;
+        if (plo < 0) plo = 0;
+        if (phi > f.rho) phi = f.rho;
+        const int tlo = (int)(plo / P2), thi = (int)(phi / P2);
+        double z = 0.0;
+        // pass 1: unnormalised sums into app, and z = sum_D prior(D) L^u(D)
+        for (int D = lane; D < q; D += 32) {
+            float s = 0.f;
+            for (int t = tlo; t <= thi; ++t) {
+                int ilo, ihi;
+                super_symbols(f, t, ilo, ihi);
+                s += f.Lp[((size_t)t * f.S2 + (i - ilo)) * q + D];
+            }
+            f.app[(size_t)i * q + D] = s;
+            z += (double)f.priors[(size_t)i * q + D] * (double)s;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (!(z > 0.0)) { bad = true; continue; }
+        const double iz = 1.0 / z;
+        // pass 2: each lane rescales the entries it wrote
+        for (int D = lane; D < q; D += 32) {
+            const size_t e = (size_t)i * q + D;
+            const double lu = (double)f.app[e];
+            f.app[e] = (float)((double)f.priors[e] * lu * iz);
+            if (f.dpriors) f.dpriors[e] = (float)(lu * iz);
+        }
+        if (grad && lane == 0) {
+            double Sw = 0.0, Sd = 0.0, Ss = 0.0;
+            for (int t = tlo; t <= thi; ++t) {
+                int ilo, ihi;
+                super_symbols(f, t, ilo, ihi);
+                const float *gp = f.Gp + ((size_t)t * f.S2 + (i - ilo)) * 3;
+                Sw += gp[0];
+                Sd += gp[1];
+                Ss += gp[2];
+            }
+            // Euler: Pd dR/dPd + Qm dR/dQm + Qs dR/dQs = n R  (R homogeneous of degree n)
+            const double Sm = ((double)n * z - Pd * Sd - Qs * Ss) / Qm;
+            g0 += (0.5 * Sw - (1.0 - Ps) * Sm - Ps * Ss) * iz;
+            g1 += (Sd - (1.0 - Ps) * Sm - Ps * Ss) * iz;
+            g2 += (-Pt * Sm + Pt * Ss) * iz;
+        }
+    }
+    if (bad && lane == 0) atomicMax(f.status, ST_ZERO);
+    if (grad && f.dchan) {
+        if (lane == 0) { red[0][warp] = g0; red[1][warp] = g1; red[2][warp] = g2; }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[threadIdx.x][w];
+            f.dchan[threadIdx.x] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (host).
+cudaError_t launch_pack(const FrameDev *frames, const uint8_t *const *rx_bytes,
+                        uint32_t *const *rx_words, int nframes, long long max_words,
+                        cudaStream_t st) {
+    if (nframes <= 0) return cudaSuccess;
+    int gx = (int)((max_words + 255) / 256);
+    if (gx > 64) gx = 64;
+    if (gx < 1) gx = 1;
+    dim3 grid(gx, nframes);
+    k_pack<<<grid, 256, 0, st>>>(frames, rx_bytes, rx_words, nframes);
+    return cudaGetLastError();
+}
+
+size_t chain_smem_bytes(const FrameDev &f) {
+    const size_t stageFloats = ((size_t)(f.chainCD + f.MN + 1) * f.MNS + 8 + 3) & ~(size_t)3;
+    return 4 * (2 * (size_t)f.Mp + kStages * stageFloats);
+}
+
+cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, size_t smem,
+                         cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_chain<<<nwork, kChainThreads, smem, st>>>(frames, work);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FrameDev *frames, int nframes, int grad, cudaStream_t st) {
+    if (nframes <= 0) return cudaSuccess;
+    k_finalize<<<nframes, kFinThreads, 0, st>>>(frames, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace mdk

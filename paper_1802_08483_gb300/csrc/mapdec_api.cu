@@ -1,0 +1,795 @@
+// Host side of libmapdec.so: argument validation, tile planning, device
+// memory, launch sequencing (optionally captured in a CUDA graph) and the
+// C ABI declared in include/mapdec.h.
+//
+// Launch sequence of one run (per wave of frames that fit the scratch budget):
+//   pack rx bits -> forward producers (lattice + W, per (n, I) class)
+//   -> forward and backward chains (one CTA per frame and direction)
+//   -> backward producers (lattice + APP / tangent partial sums)
+//   -> finalize (APPs, d logP / d prior, FP64 gradient reduction)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/mapdec.h"
+#include "mapdec_kernels.h"
+
+using namespace mdk;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+struct CudaErr {
+    cudaError_t e;
+};
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t _e = (x);                   \
+        if (_e != cudaSuccess) throw CudaErr{_e}; \
+    } while (0)
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return MAPDEC_ERR_NOMEM;
+    return MAPDEC_ERR_CUDA;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void copy_in(void *dst_dev, const void *src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return;
+    CK(cudaMemcpyAsync(dst_dev, src, bytes,
+                       is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+}
+void copy_out(void *dst, const void *src_dev, size_t bytes, cudaStream_t st) {
+    if (bytes == 0 || !dst) return;
+    CK(cudaMemcpyAsync(dst, src_dev, bytes,
+                       is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+}
+
+size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Validate one frame description; returns a MAPDEC_* status.
+int validate(int q, int n, int N, double Pi, double Pd, double Ps, int I, int xmax) {
+    if (q < 2 || n < 1 || n > 31 || N < 1 || I < 1 || I > kMaxI || xmax < 0) return MAPDEC_ERR_ARG;
+    if ((long long)q > (1ll << n)) return MAPDEC_ERR_ARG;
+    if (n * (I + 1) + 1 > kMaxMN) return MAPDEC_ERR_UNSUPPORTED;
+    if (!(Pi >= 0 && Pd >= 0 && Ps >= 0 && Ps <= 1 && Pi + Pd < 1)) return MAPDEC_ERR_ARG;
+    if (!std::isfinite(Pi) || !std::isfinite(Pd) || !std::isfinite(Ps)) return MAPDEC_ERR_ARG;
+    if ((long long)xmax > (1ll << 24)) return MAPDEC_ERR_UNSUPPORTED;
+    return MAPDEC_OK;
+}
+
+// Codebook (q*n bytes, host or device) -> packed words; checks bits and distinctness.
+int pack_codebook(const uint8_t *cb, int q, int n, std::vector<uint32_t> &out) {
+    if (!cb) return MAPDEC_ERR_ARG;
+    std::vector<uint8_t> h((size_t)q * n);
+    if (is_device_ptr(cb)) {
+        if (cudaMemcpy(h.data(), cb, h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return MAPDEC_ERR_CUDA;
+    } else {
+        std::memcpy(h.data(), cb, h.size());
+    }
+    out.assign(q, 0u);
+    std::set<uint32_t> seen;
+    for (int d = 0; d < q; ++d) {
+        uint32_t w = 0;
+        for (int r = 0; r < n; ++r) {
+            const uint8_t b = h[(size_t)d * n + r];
+            if (b > 1) return MAPDEC_ERR_ARG;
+            if (b) w |= (1u << r);
+        }
+        if (!seen.insert(w).second) return MAPDEC_ERR_ARG;  // encoding must be injective
+        out[d] = w;
+    }
+    return MAPDEC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+constexpr size_t kFwdSmemBudget = 110 * 1024;
+constexpr size_t kBwdSmemBudget = 200 * 1024;
+constexpr size_t kChainSmemBudget = 96 * 1024;
+
+struct FrameHost {
+    mapdec_frame_desc_t d;
+    std::vector<uint32_t> cw;
+    int64_t rx_off = 0;     // byte offset in the concatenated rx buffer
+    int64_t sym_off = 0;    // row offset (rows of q floats) in priors / APP buffers
+    int64_t rxw_off = 0;    // word offset in the packed rx buffer
+    int64_t cw_off = 0;     // word offset in the packed codebook buffer
+    FrameDev dev{};         // shape, constants; pointers filled per wave
+    size_t scratch_floats = 0;
+    double cost = 0.0;
+};
+
+// Fill shape-dependent fields of dev (P, S, T, nsub, ...) for received length rho.
+void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP) {
+    f.q = d.q; f.n = d.n; f.N = d.N; f.I = d.I; f.xmax = d.xmax;
+    f.M = 2 * d.xmax + 1;
+    f.Mp = (int)rup(f.M, 4);
+    f.MN = d.n * (d.I + 1) + 1;
+    f.MNS = (f.MN & 1) ? f.MN : f.MN + 1;
+    f.rho = d.rx_len;
+    f.wblk = (long long)rup((size_t)f.M * f.MNS, 4);
+    const double Pt = 1.0 - d.Pi - d.Pd;
+    double wp = 1.0;
+    for (int a = 0; a <= kMaxI; ++a) {
+        f.wpow[a] = (a <= d.I) ? (float)wp : 0.f;
+        f.wder[a] = (a >= 1 && a <= d.I) ? (float)(a * std::pow(0.5 * d.Pi, a - 1)) : 0.f;
+        wp *= 0.5 * d.Pi;
+    }
+    f.Pd = (float)d.Pd;
+    f.qsame = (float)(Pt * (1.0 - d.Ps));
+    f.qdiff = (float)(Pt * d.Ps);
+    f.dPi = d.Pi; f.dPd = d.Pd; f.dPs = d.Ps; f.dPt = Pt;
+
+    auto symbols_span = [&](long long Ppos) -> int {
+        return (int)((Ppos - 1 + 2LL * d.xmax) / d.n + 2);
+    };
+    // positions per sub-tile
+    static const int cand[] = {64, 48, 32, 24, 16, 12, 8, 6, 4, 2, 1};
+    int P = 1;
+    for (int c : cand) {
+        if (forceP > 0 && c != forceP) continue;
+        FrameDev t = f;
+        t.P = c;
+        t.S = symbols_span(c);
+        t.nsub = std::max(1, 256 / c);
+        t.S2 = symbols_span((long long)c * t.nsub);
+        if (fwd_smem_bytes(t) > kFwdSmemBudget) continue;
+        while (t.nsub > 1 && bwd_smem_bytes(t, grad) > kBwdSmemBudget) {
+            t.nsub /= 2;
+            t.S2 = symbols_span((long long)c * t.nsub);
+        }
+        if (bwd_smem_bytes(t, grad) > kBwdSmemBudget) continue;
+        P = c;
+        break;
+    }
+    f.P = P;
+    f.S = symbols_span(P);
+    f.nsub = std::max(1, 256 / P);
+    f.S2 = symbols_span((long long)P * f.nsub);
+    while (f.nsub > 1 && bwd_smem_bytes(f, grad) > kBwdSmemBudget) {
+        f.nsub /= 2;
+        f.S2 = symbols_span((long long)P * f.nsub);
+    }
+    f.T = (int)((f.rho + 1 + P - 1) / P);
+    f.T2 = (f.T + f.nsub - 1) / f.nsub;
+    // chain chunk: all states at once if it fits, else the largest power of two
+    int CD = f.M;
+    auto chain_fits = [&](int cd) {
+        FrameDev t = f;
+        t.chainCD = cd;
+        return chain_smem_bytes(t) <= kChainSmemBudget;
+    };
+    if (!chain_fits(CD)) {
+        CD = 1024;
+        while (CD > 32 && !chain_fits(CD)) CD /= 2;
+    }
+    f.chainCD = CD;
+}
+
+size_t frame_scratch_floats(const FrameDev &f, bool grad) {
+    size_t s = 0;
+    s += rup((size_t)f.N * f.wblk + 16, 64);             // W (+ tail slack for bulk copies)
+    s += rup((size_t)(f.N + 1) * f.Mp, 64) * 2;          // alpha, beta
+    s += rup((size_t)f.T2 * f.S2 * f.q, 64);             // Lp
+    if (grad) s += rup((size_t)f.T2 * f.S2 * 3, 64);     // Gp
+    return s;
+}
+
+double frame_cost(const FrameDev &f) {
+    // algorithmic flop estimate used for load balancing and reporting
+    const double cells = (f.I + 1) * f.n * (f.n + 1) / 2.0 + (f.n + 1);
+    const double lat = (double)(f.rho + 1) * f.q * cells * (2.0 * f.I + 3.0);
+    const double band = (double)f.N * f.M * f.MN;
+    return 2.0 * lat + 4.0 * band * f.q + 4.0 * band;
+}
+
+struct ClassLaunch {
+    int n, I;
+    Work *d_fwd = nullptr; int nfwd = 0; size_t smem_fwd = 0;
+    Work *d_bwd = nullptr; int nbwd = 0; size_t smem_bwd = 0;
+};
+
+struct Wave {
+    int f0 = 0, f1 = 0;
+    FrameDev *d_frames = nullptr;
+    std::vector<ClassLaunch> cls;
+    Work *d_chain = nullptr; int nchain = 0; size_t smem_chain = 0;
+    const uint8_t **d_rxptr = nullptr;
+    uint32_t **d_rxwptr = nullptr;
+    long long max_words = 0;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// batch object
+// ---------------------------------------------------------------------------
+struct mapdec_batch {
+    int nframes = 0;
+    int flags = 0;
+    bool grad = false;
+    std::vector<FrameHost> fr;
+    int64_t rx_total = 0, prior_total = 0, rxw_total = 0, cw_total = 0;
+    uint8_t *d_rx = nullptr;
+    float *d_priors = nullptr;
+    float *d_app = nullptr;
+    float *d_dpriors = nullptr;
+    double *d_loglik = nullptr;
+    double *d_dchan = nullptr;
+    int *d_status = nullptr;
+    uint32_t *d_rxw = nullptr;
+    uint32_t *d_cw = nullptr;
+    float *d_scratch = nullptr;
+    size_t scratch_floats = 0;
+    std::vector<Wave> waves;
+    std::vector<void *> allocs;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_grad = false;
+    int64_t last_launches = 0;
+    int64_t launches_per_run[2] = {0, 0};
+
+    void *dalloc(size_t bytes) {
+        void *p = nullptr;
+        CK(cudaMalloc(&p, std::max<size_t>(bytes, 16)));
+        allocs.push_back(p);
+        return p;
+    }
+    ~mapdec_batch() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        for (void *p : allocs) cudaFree(p);
+    }
+};
+
+struct mapdec {
+    int q, n, N, I, xmax;
+    double Pi, Pd, Ps;
+    std::vector<uint8_t> codebook;  // host copy
+    cudaStream_t stream = nullptr;
+    mapdec_batch *b = nullptr;      // batch of one frame, rebuilt when rho changes
+    int64_t b_rho = -1;
+    bool b_grad = false;
+    float *d_rout = nullptr;
+    size_t rout_floats = 0;
+    ~mapdec() {
+        delete b;
+        if (d_rout) cudaFree(d_rout);
+    }
+};
+
+namespace {
+
+// Build the batch: plan, allocate, upload descriptors.  Throws CudaErr.
+int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int flags,
+                int64_t budget, int forceP) {
+    b->nframes = nf;
+    b->flags = flags;
+    b->grad = (flags & MAPDEC_BATCH_GRAD) != 0;
+    b->fr.resize(nf);
+    for (int i = 0; i < nf; ++i) {
+        FrameHost &h = b->fr[i];
+        h.d = frames[i];
+        int st = validate(h.d.q, h.d.n, h.d.N, h.d.Pi, h.d.Pd, h.d.Ps, h.d.I, h.d.xmax);
+        if (st) return st;
+        const long long tau = (long long)h.d.n * h.d.N;
+        if (h.d.rx_len < 0) return MAPDEC_ERR_ARG;
+        if (std::llabs(h.d.rx_len - tau) > h.d.xmax) return MAPDEC_ERR_DRIFT_RANGE;
+        st = pack_codebook(h.d.codebook, h.d.q, h.d.n, h.cw);
+        if (st) return st;
+        h.d.codebook = nullptr;
+        plan_shape(h.dev, h.d, b->grad, (flags & MAPDEC_BATCH_PLAIN) ? 0 : forceP);
+        h.scratch_floats = frame_scratch_floats(h.dev, b->grad);
+        h.cost = frame_cost(h.dev);
+        h.rx_off = b->rx_total;
+        b->rx_total += rup(h.d.rx_len, 16);
+        h.sym_off = b->prior_total;  // element offset
+        b->prior_total += (int64_t)h.d.N * h.d.q;
+        h.rxw_off = b->rxw_total;
+        b->rxw_total += (h.d.rx_len + 31) / 32 + 4;
+        h.cw_off = b->cw_total;
+        b->cw_total += h.d.q;
+    }
+    // resident buffers
+    b->d_rx = (uint8_t *)b->dalloc(b->rx_total + 64);
+    b->d_priors = (float *)b->dalloc(b->prior_total * 4);
+    b->d_app = (float *)b->dalloc(b->prior_total * 4);
+    if (b->grad) {
+        b->d_dpriors = (float *)b->dalloc(b->prior_total * 4);
+        b->d_dchan = (double *)b->dalloc((size_t)nf * 3 * 8);
+    }
+    b->d_loglik = (double *)b->dalloc((size_t)nf * 8);
+    b->d_status = (int *)b->dalloc((size_t)nf * 4);
+    b->d_rxw = (uint32_t *)b->dalloc(b->rxw_total * 4);
+    b->d_cw = (uint32_t *)b->dalloc(b->cw_total * 4);
+    {
+        std::vector<uint32_t> cwall(b->cw_total);
+        for (auto &h : b->fr) std::copy(h.cw.begin(), h.cw.end(), cwall.begin() + h.cw_off);
+        CK(cudaMemcpy(b->d_cw, cwall.data(), cwall.size() * 4, cudaMemcpyHostToDevice));
+    }
+    // scratch budget and waves (frames kept in order; a wave is a contiguous range)
+    size_t freeb = 0, totb = 0;
+    CK(cudaMemGetInfo(&freeb, &totb));
+    size_t bud = budget > 0 ? (size_t)budget : (size_t)(0.6 * (double)freeb);
+    size_t maxf = 0;
+    for (auto &h : b->fr) maxf = std::max(maxf, h.scratch_floats);
+    if (maxf * 4 > bud) bud = maxf * 4;  // at least one frame per wave
+    {
+        size_t acc = 0;
+        Wave w;
+        w.f0 = 0;
+        for (int i = 0; i < nf; ++i) {
+            if (acc + b->fr[i].scratch_floats > bud / 4 && i > w.f0) {
+                w.f1 = i;
+                b->waves.push_back(w);
+                w = Wave();
+                w.f0 = i;
+                acc = 0;
+            }
+            acc += b->fr[i].scratch_floats;
+            b->scratch_floats = std::max(b->scratch_floats, acc);
+        }
+        w.f1 = nf;
+        b->waves.push_back(w);
+    }
+    b->d_scratch = (float *)b->dalloc(b->scratch_floats * 4 + 256);
+    // per-wave descriptors and work tables
+    for (auto &w : b->waves) {
+        size_t off = 0;
+        std::vector<FrameDev> devs;
+        std::vector<const uint8_t *> rxp;
+        std::vector<uint32_t *> rxwp;
+        std::map<std::pair<int, int>, std::vector<int>> byclass;
+        for (int i = w.f0; i < w.f1; ++i) {
+            FrameHost &h = b->fr[i];
+            FrameDev f = h.dev;
+            f.rxbits = b->d_rxw + h.rxw_off;
+            f.cw = b->d_cw + h.cw_off;
+            f.priors = b->d_priors + h.sym_off;
+            float *base = b->d_scratch + off;
+            size_t o = 0;
+            f.W = base + o; o += rup((size_t)f.N * f.wblk + 16, 64);
+            f.alpha = base + o; o += rup((size_t)(f.N + 1) * f.Mp, 64);
+            f.beta = base + o; o += rup((size_t)(f.N + 1) * f.Mp, 64);
+            f.Lp = base + o; o += rup((size_t)f.T2 * f.S2 * f.q, 64);
+            f.Gp = nullptr;
+            if (b->grad) { f.Gp = base + o; o += rup((size_t)f.T2 * f.S2 * 3, 64); }
+            off += o;
+            f.Rout = nullptr;
+            f.app = b->d_app + h.sym_off;
+            f.dpriors = b->grad ? b->d_dpriors + h.sym_off : nullptr;
+            f.loglik = b->d_loglik + i;
+            f.dchan = b->grad ? b->d_dchan + 3 * (size_t)i : nullptr;
+            f.status = b->d_status + i;
+            h.dev = f;
+            devs.push_back(f);
+            rxp.push_back(b->d_rx + h.rx_off);
+            rxwp.push_back(b->d_rxw + h.rxw_off);
+            w.max_words = std::max<long long>(w.max_words, (h.d.rx_len + 31) / 32 + 3);
+            byclass[{h.d.n, h.d.I}].push_back(i - w.f0);
+        }
+        const int nw = w.f1 - w.f0;
+        w.d_frames = (FrameDev *)b->dalloc(sizeof(FrameDev) * nw);
+        CK(cudaMemcpy(w.d_frames, devs.data(), sizeof(FrameDev) * nw, cudaMemcpyHostToDevice));
+        w.d_rxptr = (const uint8_t **)b->dalloc(sizeof(void *) * nw);
+        w.d_rxwptr = (uint32_t **)b->dalloc(sizeof(void *) * nw);
+        CK(cudaMemcpy(w.d_rxptr, rxp.data(), sizeof(void *) * nw, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(w.d_rxwptr, rxwp.data(), sizeof(void *) * nw, cudaMemcpyHostToDevice));
+        // chains: costliest frames first so long chains start early
+        std::vector<int> order(nw);
+        for (int k = 0; k < nw; ++k) order[k] = k;
+        std::sort(order.begin(), order.end(), [&](int a, int c) {
+            return (double)devs[a].N * devs[a].M * devs[a].MN >
+                   (double)devs[c].N * devs[c].M * devs[c].MN;
+        });
+        std::vector<Work> chain;
+        size_t csm = 0;
+        for (int k : order) {
+            chain.push_back({k, 0});
+            chain.push_back({k, 1});
+            csm = std::max(csm, chain_smem_bytes(devs[k]));
+        }
+        w.nchain = (int)chain.size();
+        w.smem_chain = csm;
+        w.d_chain = (Work *)b->dalloc(sizeof(Work) * chain.size());
+        CK(cudaMemcpy(w.d_chain, chain.data(), sizeof(Work) * chain.size(), cudaMemcpyHostToDevice));
+        for (auto &kv : byclass) {
+            ClassLaunch c;
+            c.n = kv.first.first;
+            c.I = kv.first.second;
+            std::vector<Work> fw, bw;
+            for (int k : kv.second) {
+                const FrameDev &f = devs[k];
+                for (int t = 0; t < f.T; ++t) fw.push_back({k, t});
+                for (int t = 0; t < f.T2; ++t) bw.push_back({k, t});
+                c.smem_fwd = std::max(c.smem_fwd, fwd_smem_bytes(f));
+                c.smem_bwd = std::max(c.smem_bwd, bwd_smem_bytes(f, b->grad));
+            }
+            c.nfwd = (int)fw.size();
+            c.nbwd = (int)bw.size();
+            c.d_fwd = (Work *)b->dalloc(sizeof(Work) * fw.size());
+            c.d_bwd = (Work *)b->dalloc(sizeof(Work) * bw.size());
+            CK(cudaMemcpy(c.d_fwd, fw.data(), sizeof(Work) * fw.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c.d_bwd, bw.data(), sizeof(Work) * bw.size(), cudaMemcpyHostToDevice));
+            w.cls.push_back(c);
+        }
+    }
+    return MAPDEC_OK;
+}
+
+// Enqueue one full run on b->stream.  Throws CudaErr.
+int64_t enqueue_run(mapdec_batch *b, bool grad) {
+    cudaStream_t st = b->stream;
+    int64_t launches = 0;
+    CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->nframes * 4, st));
+    for (auto &w : b->waves) {
+        const int nw = w.f1 - w.f0;
+        CK(launch_pack(w.d_frames, w.d_rxptr, w.d_rxwptr, nw, w.max_words, st));
+        ++launches;
+        for (auto &c : w.cls) {
+            CK(launch_fwd(c.n, c.I, w.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
+            ++launches;
+        }
+        CK(launch_chain(w.d_frames, w.d_chain, w.nchain, w.smem_chain, st));
+        ++launches;
+        for (auto &c : w.cls) {
+            CK(launch_bwd(c.n, c.I, grad, w.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
+            ++launches;
+        }
+        CK(launch_finalize(w.d_frames, nw, grad ? 1 : 0, st));
+        ++launches;
+    }
+    return launches;
+}
+
+int run_batch(mapdec_batch *b, bool grad) {
+    if (grad && !b->grad) return MAPDEC_ERR_ARG;
+    const bool use_graph = (b->flags & MAPDEC_BATCH_GRAPH) && !(b->flags & MAPDEC_BATCH_PLAIN);
+    if (!use_graph) {
+        b->last_launches = enqueue_run(b, grad);
+        return MAPDEC_OK;
+    }
+    if (!b->gexec || b->graph_grad != grad) {
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int64_t l = 0;
+        try {
+            l = enqueue_run(b, grad);
+        } catch (CudaErr &e) {
+            cudaStreamEndCapture(b->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        CK(cudaStreamEndCapture(b->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        b->graph_grad = grad;
+        b->launches_per_run[grad ? 1 : 0] = l;
+    }
+    CK(cudaGraphLaunch(b->gexec, b->stream));
+    b->last_launches = b->launches_per_run[grad ? 1 : 0];
+    return MAPDEC_OK;
+}
+
+int worst_status(mapdec_batch *b) {
+    std::vector<int> st(b->nframes);
+    CK(cudaMemcpyAsync(st.data(), b->d_status, st.size() * 4, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    int w = 0;
+    for (int s : st) w = std::max(w, s);
+    return w;
+}
+
+// Copy inputs (host or device) into the resident buffers.
+void load_inputs(mapdec_batch *b, const uint8_t *rx_all, const float *priors_all) {
+    cudaStream_t st = b->stream;
+    if (rx_all) {
+        // caller buffer is densely concatenated (no padding); resident buffer is padded
+        int64_t src = 0;
+        const bool dev = is_device_ptr(rx_all);
+        for (auto &h : b->fr) {
+            CK(cudaMemcpyAsync(b->d_rx + h.rx_off, rx_all + src, h.d.rx_len,
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+            src += h.d.rx_len;
+        }
+    }
+    if (priors_all) {
+        copy_in(b->d_priors, priors_all, (size_t)b->prior_total * 4, st);
+    } else {
+        // uniform priors: 1/q per frame
+        std::vector<float> u((size_t)b->prior_total);
+        for (auto &h : b->fr)
+            std::fill(u.begin() + h.sym_off, u.begin() + h.sym_off + (size_t)h.d.N * h.d.q,
+                      1.0f / (float)h.d.q);
+        CK(cudaMemcpyAsync(b->d_priors, u.data(), u.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *mapdec_strerror(int s) {
+    switch (s) {
+        case MAPDEC_OK: return "ok";
+        case MAPDEC_ERR_ARG: return "invalid argument";
+        case MAPDEC_ERR_DRIFT_RANGE: return "received length outside the drift limit";
+        case MAPDEC_ERR_ZERO_PROB: return "no channel path within the drift limits explains the received bits";
+        case MAPDEC_ERR_NOMEM: return "out of memory";
+        case MAPDEC_ERR_CUDA: return "CUDA error or no usable device";
+        case MAPDEC_ERR_TIMEOUT: return "device-side wait timed out";
+        case MAPDEC_ERR_UNSUPPORTED: return "parameters outside the supported range";
+        default: return "unknown status";
+    }
+}
+
+int mapdec_batch_create(mapdec_batch_t **out, const mapdec_frame_desc_t *frames, int num_frames,
+                        int flags, int64_t mem_budget_bytes) {
+    if (!out || !frames || num_frames < 1) return MAPDEC_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return MAPDEC_ERR_CUDA;
+    }
+    mapdec_batch *b = new (std::nothrow) mapdec_batch();
+    if (!b) return MAPDEC_ERR_NOMEM;
+    int forceP = 0;
+    if (const char *e = std::getenv("MAPDEC_FORCE_P")) forceP = std::atoi(e);
+    int st;
+    try {
+        st = build_batch(b, frames, num_frames, flags, mem_budget_bytes, forceP);
+    } catch (CudaErr &e) {
+        cudaGetLastError();
+        st = map_cuda(e.e);
+    } catch (std::bad_alloc &) {
+        st = MAPDEC_ERR_NOMEM;
+    }
+    if (st != MAPDEC_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return MAPDEC_OK;
+}
+
+int mapdec_batch_layout(mapdec_batch_t *b, int64_t *rx_offsets, int64_t *sym_offsets,
+                        int64_t *rx_total, int64_t *prior_elems_total) {
+    if (!b) return MAPDEC_ERR_ARG;
+    int64_t acc = 0;
+    for (int i = 0; i < b->nframes; ++i) {
+        if (rx_offsets) rx_offsets[i] = acc;
+        acc += b->fr[i].d.rx_len;
+        if (sym_offsets) sym_offsets[i] = b->fr[i].sym_off;
+    }
+    if (rx_total) *rx_total = acc;
+    if (prior_elems_total) *prior_elems_total = b->prior_total;
+    return MAPDEC_OK;
+}
+
+int mapdec_batch_buffers(mapdec_batch_t *b, uint8_t **rx_dev, float **priors_dev, float **app_dev,
+                         double **loglik_dev) {
+    if (!b) return MAPDEC_ERR_ARG;
+    // The resident rx buffer pads every frame to 16 bytes; callers filling it in
+    // place must use mapdec_batch_rx_offset.
+    if (rx_dev) *rx_dev = b->d_rx;
+    if (priors_dev) *priors_dev = b->d_priors;
+    if (app_dev) *app_dev = b->d_app;
+    if (loglik_dev) *loglik_dev = b->d_loglik;
+    return MAPDEC_OK;
+}
+
+int64_t mapdec_batch_rx_offset(mapdec_batch_t *b, int frame) {
+    if (!b || frame < 0 || frame >= b->nframes) return -1;
+    return b->fr[frame].rx_off;
+}
+
+int mapdec_batch_run(mapdec_batch_t *b) {
+    if (!b) return MAPDEC_ERR_ARG;
+    try {
+        return run_batch(b, false);
+    } catch (CudaErr &e) {
+        cudaGetLastError();
+        return map_cuda(e.e);
+    }
+}
+
+int mapdec_batch_sync(mapdec_batch_t *b) {
+    if (!b) return MAPDEC_ERR_ARG;
+    try {
+        return worst_status(b);
+    } catch (CudaErr &e) {
+        cudaGetLastError();
+        return map_cuda(e.e);
+    }
+}
+
+int mapdec_batch_status(mapdec_batch_t *b, int *status_per_frame) {
+    if (!b || !status_per_frame) return MAPDEC_ERR_ARG;
+    if (cudaMemcpy(status_per_frame, b->d_status, (size_t)b->nframes * 4,
+                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return MAPDEC_ERR_CUDA;
+    }
+    return MAPDEC_OK;
+}
+
+int mapdec_batch_decode(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
+                        float *app_all, double *loglik_all) {
+    if (!b || !rx_all) return MAPDEC_ERR_ARG;
+    try {
+        load_inputs(b, rx_all, priors_all);
+        int st = run_batch(b, false);
+        if (st) return st;
+        copy_out(app_all, b->d_app, (size_t)b->prior_total * 4, b->stream);
+        copy_out(loglik_all, b->d_loglik, (size_t)b->nframes * 8, b->stream);
+        return worst_status(b);
+    } catch (CudaErr &e) {
+        cudaGetLastError();
+        return map_cuda(e.e);
+    }
+}
+
+int mapdec_batch_loglik_grad(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
+                             double *dchan_all, float *dpriors_all, double *loglik_all) {
+    if (!b || !rx_all) return MAPDEC_ERR_ARG;
+    if (!b->grad) return MAPDEC_ERR_ARG;
+    try {
+        load_inputs(b, rx_all, priors_all);
+        int st = run_batch(b, true);
+        if (st) return st;
+        copy_out(dchan_all, b->d_dchan, (size_t)b->nframes * 3 * 8, b->stream);
+        copy_out(dpriors_all, b->d_dpriors, (size_t)b->prior_total * 4, b->stream);
+        copy_out(loglik_all, b->d_loglik, (size_t)b->nframes * 8, b->stream);
+        return worst_status(b);
+    } catch (CudaErr &e) {
+        cudaGetLastError();
+        return map_cuda(e.e);
+    }
+}
+
+int mapdec_batch_set_stream(mapdec_batch_t *b, void *s) {
+    if (!b) return MAPDEC_ERR_ARG;
+    b->stream = (cudaStream_t)s;
+    return MAPDEC_OK;
+}
+
+void mapdec_batch_destroy(mapdec_batch_t *b) { delete b; }
+
+int64_t mapdec_batch_last_launches(mapdec_batch_t *b) { return b ? b->last_launches : -1; }
+
+// ---------------------------------------------------------------------------
+// single-frame handle
+// ---------------------------------------------------------------------------
+int mapdec_create(mapdec_t **out, int q, int n, const uint8_t *codebook, int N, double Pi,
+                  double Pd, double Ps, int I, int xmax) {
+    if (!out) return MAPDEC_ERR_ARG;
+    *out = nullptr;
+    int st = validate(q, n, N, Pi, Pd, Ps, I, xmax);
+    if (st) return st;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return MAPDEC_ERR_CUDA;
+    }
+    std::vector<uint32_t> cw;
+    st = pack_codebook(codebook, q, n, cw);
+    if (st) return st;
+    mapdec *h = new (std::nothrow) mapdec();
+    if (!h) return MAPDEC_ERR_NOMEM;
+    h->q = q; h->n = n; h->N = N; h->I = I; h->xmax = xmax;
+    h->Pi = Pi; h->Pd = Pd; h->Ps = Ps;
+    h->codebook.resize((size_t)q * n);
+    for (int d = 0; d < q; ++d)
+        for (int r = 0; r < n; ++r) h->codebook[(size_t)d * n + r] = (cw[d] >> r) & 1u;
+    *out = h;
+    return MAPDEC_OK;
+}
+
+int mapdec_set_stream(mapdec_t *h, void *s) {
+    if (!h) return MAPDEC_ERR_ARG;
+    h->stream = (cudaStream_t)s;
+    if (h->b) h->b->stream = h->stream;
+    return MAPDEC_OK;
+}
+
+static int ensure_single(mapdec_t *h, int64_t rho, bool grad) {
+    const long long tau = (long long)h->n * h->N;
+    if (rho < 0) return MAPDEC_ERR_ARG;
+    if (std::llabs(rho - tau) > h->xmax) return MAPDEC_ERR_DRIFT_RANGE;
+    if (h->b && h->b_rho == rho && (h->b_grad || !grad)) return MAPDEC_OK;
+    delete h->b;
+    h->b = nullptr;
+    mapdec_frame_desc_t d;
+    d.q = h->q; d.n = h->n; d.N = h->N; d.I = h->I; d.xmax = h->xmax;
+    d.Pi = h->Pi; d.Pd = h->Pd; d.Ps = h->Ps;
+    d.codebook = h->codebook.data();
+    d.rx_len = rho;
+    mapdec_batch_t *b = nullptr;
+    int st = mapdec_batch_create(&b, &d, 1, MAPDEC_BATCH_PLAIN | (grad ? MAPDEC_BATCH_GRAD : 0), 0);
+    if (st) return st;
+    b->stream = h->stream;
+    h->b = b;
+    h->b_rho = rho;
+    h->b_grad = grad;
+    return MAPDEC_OK;
+}
+
+int mapdec_decode(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *priors,
+                  float *app_out, double *loglik_out) {
+    if (!h || (!rx && rx_len > 0)) return MAPDEC_ERR_ARG;
+    int st = ensure_single(h, rx_len, false);
+    if (st) return st;
+    return mapdec_batch_decode(h->b, rx ? rx : (const uint8_t *)"", priors, app_out, loglik_out);
+}
+
+int mapdec_loglik_grad(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *priors,
+                       double *dlogp_dchan, float *dlogp_dpriors, double *loglik_out) {
+    if (!h || (!rx && rx_len > 0)) return MAPDEC_ERR_ARG;
+    if (!(h->Pd > 0) || !((1.0 - h->Pi - h->Pd) * (1.0 - h->Ps) > 0)) return MAPDEC_ERR_UNSUPPORTED;
+    int st = ensure_single(h, rx_len, true);
+    if (st) return st;
+    return mapdec_batch_loglik_grad(h->b, rx ? rx : (const uint8_t *)"", priors, dlogp_dchan,
+                                    dlogp_dpriors, loglik_out);
+}
+
+int mapdec_receiver_metric(mapdec_t *h, const uint8_t *rx, int64_t rx_len, float *R_out) {
+    if (!h || !R_out || (!rx && rx_len > 0)) return MAPDEC_ERR_ARG;
+    int st = ensure_single(h, rx_len, false);
+    if (st) return st;
+    mapdec_batch *b = h->b;
+    try {
+        load_inputs(b, rx ? rx : (const uint8_t *)"", nullptr);
+        const FrameHost &fh = b->fr[0];
+        const size_t nfl = (size_t)(rx_len + 1) * h->q * fh.dev.MN;
+        if (h->rout_floats < nfl) {
+            if (h->d_rout) cudaFree(h->d_rout);
+            h->d_rout = nullptr;
+            CK(cudaMalloc(&h->d_rout, nfl * 4));
+            h->rout_floats = nfl;
+        }
+        Wave &w = b->waves[0];
+        FrameDev f = fh.dev;
+        f.Rout = h->d_rout;
+        CK(cudaMemcpyAsync(w.d_frames, &f, sizeof(FrameDev), cudaMemcpyHostToDevice, b->stream));
+        CK(launch_pack(w.d_frames, w.d_rxptr, w.d_rxwptr, 1, w.max_words, b->stream));
+        CK(launch_rmetric(h->n, h->I, w.d_frames, (long long)(rx_len + 1) * h->q, b->stream));
+        FrameDev f0 = fh.dev;
+        CK(cudaMemcpyAsync(w.d_frames, &f0, sizeof(FrameDev), cudaMemcpyHostToDevice, b->stream));
+        copy_out(R_out, h->d_rout, nfl * 4, b->stream);
+        CK(cudaStreamSynchronize(b->stream));
+        return MAPDEC_OK;
+    } catch (CudaErr &e) {
+        cudaGetLastError();
+        return map_cuda(e.e);
+    }
+}
+
+void mapdec_destroy(mapdec_t *h) { delete h; }
+
+}  // extern "C"

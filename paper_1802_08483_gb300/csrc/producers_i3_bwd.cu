@@ -1,0 +1,16 @@
+// Backward producer specialisations (APP partial sums) for I = 3, n = 1..12.
+#define MAPDEC_IB 3
+#include "producers_inst.cuh"
+
+namespace mdk {
+
+cudaError_t launch_bwd_I3_plain(int n, const FrameDev *frames, const Work *work, int nwork,
+                                  size_t smem, cudaStream_t st) {
+    const bool grad = false;
+    switch (n) {
+        MAPDEC_FOR_N(MAPDEC_CASE_BWDX)
+        default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace mdk

@@ -1,0 +1,61 @@
+// Launch templates for one (n, I) specialisation of the producers.
+#pragma once
+
+#include "mapdec_kernels.h"
+#include "producers.cuh"
+
+namespace mdk {
+
+constexpr int kMaxDynSmem = 227 * 1024;
+
+template <int NB, int IB>
+cudaError_t launch_fwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_fwd<NB, IB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kMaxDynSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (nw <= 0) return cudaSuccess;
+    k_fwd<NB, IB><<<nw, kThreads, smem, st>>>(fr, w);
+    return cudaGetLastError();
+}
+
+template <int NB, int IB, bool GRAD>
+cudaError_t launch_bwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_bwd<NB, IB, GRAD>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kMaxDynSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (nw <= 0) return cudaSuccess;
+    k_bwd<NB, IB, GRAD><<<nw, kThreads, smem, st>>>(fr, w);
+    return cudaGetLastError();
+}
+
+template <int NB, int IB>
+cudaError_t launch_rmetric_t(const FrameDev *fr, long long nthreads, cudaStream_t st) {
+    if (nthreads <= 0) return cudaSuccess;
+    const long long blocks = (nthreads + kThreads - 1) / kThreads;
+    k_rmetric<NB, IB><<<(unsigned)blocks, kThreads, 0, st>>>(fr);
+    return cudaGetLastError();
+}
+
+}  // namespace mdk
+
+// Per-I dispatch over n = 1..12.
+#define MAPDEC_CASE_FWD(NV) case NV: return launch_fwd_t<NV, MAPDEC_IB>(frames, work, nwork, smem, st);
+#define MAPDEC_CASE_BWD(NV)                                                            \
+    case NV:                                                                           \
+        return grad ? launch_bwd_t<NV, MAPDEC_IB, true>(frames, work, nwork, smem, st) \
+                    : launch_bwd_t<NV, MAPDEC_IB, false>(frames, work, nwork, smem, st);
+// grad is a compile-time constant in each unit, so only one variant is instantiated
+#define MAPDEC_CASE_BWDX(NV) \
+    case NV: return launch_bwd_t<NV, MAPDEC_IB, grad>(frames, work, nwork, smem, st);
+#define MAPDEC_CASE_RM(NV) case NV: return launch_rmetric_t<NV, MAPDEC_IB>(frame, nthreads, st);
+#define MAPDEC_FOR_N(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)

@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every symbol include/mapdec.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+
+import pytest
+
+from paper_1802_08483_gb300 import build as libbuild
+from paper_1802_08483_gb300 import mapdec
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return mapdec.load()
+
+
+def test_header_symbols_exported(lib):
+    syms = mapdec.header_symbols()
+    assert "mapdec_create" in syms and "mapdec_decode" in syms and "mapdec_loglik_grad" in syms
+    raw = ctypes.CDLL(mapdec.LIB_PATH)
+    for s in syms:
+        assert hasattr(raw, s), f"missing export {s}"
+    # every exported entry point has a binding of the same name
+    for s in syms:
+        assert hasattr(mapdec, s), f"no python binding named {s}"
+
+
+def test_strerror_names_every_status(lib):
+    for st in range(8):
+        assert mapdec.mapdec_strerror(st) != "unknown status"
+    assert mapdec.mapdec_strerror(99) == "unknown status"
+
+
+def test_header_documents_every_entry_point():
+    import re
+    txt = open(mapdec.HEADER).read()
+    for s in mapdec.header_symbols():
+        m = re.search(r"^[A-Za-z_][A-Za-z_0-9 ]*\**\s*\**" + s + r"\(", txt, flags=re.M)
+        assert m, f"no declaration of {s}"
+        before = txt[:m.start()].rstrip()
+        assert before.endswith("*/"), f"{s} lacks a comment right above its declaration"
+
+
+def test_library_does_not_link_oracle(lib):
+    # the decoder library must not depend on the oracle
+    data = open(mapdec.LIB_PATH, "rb").read()
+    assert b"orc_decode" not in data and b"liboracle" not in data
+
+
+@pytest.mark.skipif(os.environ.get("CUDA_VISIBLE_DEVICES", None) is None and
+                    __import__("torch").cuda.is_available(), reason="GPU present")
+def test_no_gpu_fails_loudly(lib):
+    """Without a usable device, create reports MAPDEC_ERR_CUDA (no CPU fallback)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    import numpy as np
+    cb = np.array([[0, 0], [1, 1]], np.uint8)
+    with pytest.raises(mapdec.MapDecError) as e:
+        mapdec.mapdec_create(2, 2, cb, 4, 0.01, 0.01, 0.0, 1, 4)
+    assert e.value.status == mapdec.MAPDEC_ERR_CUDA
