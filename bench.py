@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched BSID MAP decoder on one or more GPUs.
+
+Workload (default): 4096 mixed frames per GPU -- N ~ U[100, 4000], (q, n) in
+{(2,4),(8,6),(16,10),(32,8),(64,12)}, Pi = Pd log-uniform in [1e-3, 0.1],
+Ps ~ U[0, 0.01], I = 2, xmax = ceil(6 sqrt(N n (Pi + Pd))), Dirichlet(1)
+priors -- decoded in one batch replayed as a CUDA graph.  One step = the whole
+decode (receiver metric, forward/backward recursions, APPs, log-likelihoods)
+of every frame.  Metric: decoded information bits per second (sum over frames
+of N log2 q, divided by the step time).
+
+Multi-GPU (torchrun): every rank decodes its own 4096 frames (weak scaling);
+no collective touches the data path.  `--impl reference` times the FP64 CPU
+oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1802_08483_gb300 import synth  # noqa: E402
+
+METRIC = "decoded info bits/s on 1 GB300, batched FP32 vs plain FP32, APP err<=1e-4 vs FP64"
+UNIT = "bits/s"
+FRAMES_PER_GPU = 4096
+
+
+# ---------------------------------------------------------------------------
+# work accounting
+# ---------------------------------------------------------------------------
+def lattice_cells(n, I):
+    return (I + 1) * n * (n + 1) // 2 + n
+
+
+def valid_transitions(fr) -> int:
+    """Number of (i, s', j) with start position in [0, rho], end drift inside the
+    limits and window inside the received sequence."""
+    n, N, M, x, rho = fr.n, fr.N, 2 * fr.xmax + 1, fr.xmax, fr.rho
+    MN = n * (fr.I + 1) + 1
+    i = np.arange(N, dtype=np.int64)
+    tot = 0
+    for j in range(MN):
+        lo = np.maximum.reduce([np.zeros_like(i), x - n * i, np.full_like(i, n - j)])
+        hi = np.minimum.reduce([np.full_like(i, M - 1), rho - n * i + x - j,
+                                np.full_like(i, M - 1 - j + n)])
+        tot += int(np.maximum(hi - lo + 1, 0).sum())
+    return tot
+
+
+def frame_flops(fr) -> dict:
+    """Algorithmic FP32 flops per phase for one frame (one FMA = 2 flops)."""
+    lat = (fr.rho + 1) * fr.q * lattice_cells(fr.n, fr.I) * (2 * fr.I + 3)
+    V = valid_transitions(fr)
+    return {"forward": lat + 2 * fr.q * V, "chains": 4 * V, "backward": lat + 2 * fr.q * V,
+            "lattice": lat, "V": V}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reported baseline / reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_frame(args):
+    cfg, idx = args
+    import oracle
+    fr = synth.config_frame(cfg, idx)
+    t = time.time()
+    oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                  priors=fr.priors_or_uniform())
+    return idx, fr.info_bits, time.time() - t
+
+
+def oracle_cost(q, n, N, xmax, I=2):
+    M = 2 * xmax + 1
+    MN = n * (I + 1) + 1
+    return 3.0 * N * M * q * MN
+
+
+def oracle_sample(frame_offset: int, budget_units: float, max_frame_units: float):
+    """Frames of the workload in index order, skipping any whose oracle cost exceeds
+    max_frame_units, until budget_units is used."""
+    picked, used, f = [], 0.0, frame_offset
+    while used < budget_units and f < frame_offset + FRAMES_PER_GPU:
+        q, n, N, xmax = synth.c3_frame_shape(f)
+        c = oracle_cost(q, n, N, xmax)
+        if c <= max_frame_units:
+            picked.append(f)
+            used += c
+        f += 1
+    return picked
+
+
+def run_oracle(frames_idx, cores):
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    t0 = time.time()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_frame, [(3, f) for f in frames_idx], chunksize=1)
+    wall = time.time() - t0
+    bits = sum(r[1] for r in res)
+    return bits, wall
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=FRAMES_PER_GPU,
+                    help="frames per GPU (the workload is 4096; smaller only for profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    n_gpus = max(args.gpus, world)
+    frame_offset = rank * FRAMES_PER_GPU
+    steps, warmup = max(1, args.steps), max(3, args.warmup)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cores = host_cores()
+        per_step = []
+        bits_tot = 0.0
+        budget = 1.5e9 * cores * min(args.oracle_seconds, 60.0) / max(1, steps + warmup) * 2
+        sample = oracle_sample(0, budget, 1.5e9 * 20)
+        for s in range(warmup + steps):
+            bits, wall = run_oracle(sample, cores)
+            if s >= warmup:
+                per_step.append(wall)
+                bits_tot = bits
+        t = statistics.mean(per_step)
+        val = bits_tot / t
+        line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": n_gpus, "steps": steps,
+                "warmup": warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": f"mixed-4096: FP64 CPU oracle on a sample of "
+                                       f"{len(sample)} frames per step"},
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"workload frames {sample[:8]}{'...' if len(sample) > 8 else ''} "
+                                           f"({len(sample)} frames, {bits_tot:.0f} info bits)"},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    # ---- CPU baseline first (spawned pool, before any GPU work) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        sample = oracle_sample(0, 1.2e9 * cores * args.oracle_seconds / 2, 1.2e9 * 25)
+        bits, wall = run_oracle(sample, cores)
+        cpu = {"value": bits / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{len(sample)} frames of the mixed workload in index order "
+                         f"(frames whose oracle cost exceeds ~25 core-s skipped), "
+                         f"{bits:.0f} info bits in {wall:.1f} s"}
+
+    import torch
+    from paper_1802_08483_gb300 import build as libbuild
+    from paper_1802_08483_gb300 import mapdec
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    libbuild.build()
+    mapdec.load()
+
+    # ---- workload ----
+    t0 = time.time()
+    frames = [synth.config_frame(3, frame_offset + f) for f in range(args.frames)]
+    gen_s = time.time() - t0
+    bits_per_step = sum(f.info_bits for f in frames)
+    flops = {"forward": 0, "chains": 0, "backward": 0, "lattice": 0, "V": 0}
+    for f in frames:
+        for k, v in frame_flops(f).items():
+            flops[k] += v
+
+    b = mapdec.Batch(frames, flags=mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_TIMING)
+    rx_all, pr_all = b.concat_inputs()
+    # stage inputs into the batch's resident device buffers (one decode call)
+    st, app0, ll0 = b.decode(rx_all, pr_all)
+    if st != 0:
+        raise RuntimeError(f"decode failed: {mapdec.mapdec_strerror(st)}")
+    stream = torch.cuda.current_stream()
+    mapdec.mapdec_batch_set_stream(b.b, stream.cuda_stream)
+
+    def one_step():
+        rc = mapdec.mapdec_batch_run(b.b)
+        if rc != 0:
+            raise RuntimeError(mapdec.mapdec_strerror(rc))
+
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    phase_tot = np.zeros(5)
+    launches = 0
+    ev0.record(stream)
+    for _ in range(steps):
+        one_step()
+        launches += mapdec.mapdec_batch_last_launches(b.b)
+        phase_tot += mapdec.mapdec_batch_phase_ms(b.b)  # events recorded inside the graph
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / steps
+    status = mapdec.mapdec_batch_sync(b.b)
+    if status != 0:
+        raise RuntimeError(f"decode status {mapdec.mapdec_strerror(status)}")
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        bt = torch.tensor([bits_per_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+        total_bits = float(bt.item())
+    else:
+        total_bits = bits_per_step
+    value = total_bits / (ms / 1e3)
+    phase_ms = phase_tot / steps
+
+    # ---- roofline of the dominant phase (FP32 CUDA-core arithmetic) ----
+    props = torch.cuda.get_device_properties(local_rank)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    names = list(mapdec.PHASES)
+    dom = int(np.argmax(phase_ms))
+    dom_name = names[dom]
+    dom_flops = flops.get(dom_name, 0)
+    achieved = dom_flops / (phase_ms[dom] / 1e3) / 1e12 if phase_ms[dom] > 0 else 0.0
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = prof.get(dom_name)
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak if fp32_peak else None, "traffic": traffic,
+                "kernel": f"{dom_name} phase", "phase_ms": {names[k]: round(float(phase_ms[k]), 3)
+                                                             for k in range(5)},
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                               f"{sm_max:.0f} MHz"}
+    total_alg = flops["forward"] + flops["chains"] + flops["backward"]
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        rx_h = torch.from_numpy(rx_all).pin_memory()
+        pr_h = torch.from_numpy(pr_all).pin_memory()
+        app_h = torch.empty(b.prior_total, dtype=torch.float32).pin_memory()
+        ll_h = torch.empty(b.nf, dtype=torch.float64).pin_memory()
+        e_steps = max(1, min(steps, 3))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(e_steps):
+            rc = mapdec.mapdec_batch_decode(b.b, rx_h, pr_h, app_h, ll_h)
+            if rc != 0:
+                raise RuntimeError(mapdec.mapdec_strerror(rc))
+        e_s = (time.perf_counter() - t1) / e_steps
+        e2e = {"value": bits_per_step / e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(rx_all.nbytes + pr_all.nbytes),
+               "d2h_bytes_per_step": int(b.prior_total * 4 + b.nf * 8)}
+
+    # ---- plain comparator: one frame per launch sequence, default tiles, no graph ----
+    plain = None
+    if not args.no_plain and rank == 0:
+        sub = frames[:64]
+        decs = [mapdec.Decoder.for_frame(f) for f in sub]
+        for d, f in zip(decs, sub):  # first call plans and allocates; not timed
+            d.decode(f.rx, f.priors)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for d, f in zip(decs, sub):
+            d.decode(f.rx, f.priors)
+        p_s = time.perf_counter() - t1
+        plain = {"value": sum(f.info_bits for f in sub) / p_s, "unit": UNIT,
+                 "frames": len(sub), "note": "first 64 frames decoded one at a time"}
+        for d in decs:
+            d.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_gpus, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"mixed-{args.frames}: N~U[100,4000], (q,n) in "
+                                   "{(2,4),(8,6),(16,10),(32,8),(64,12)}, Pi=Pd log-U[1e-3,0.1], "
+                                   "Ps~U[0,0.01], I=2, xmax=ceil(6 sqrt(N n (Pi+Pd))), "
+                                   "Dirichlet(1) priors; one CUDA-graph batch per GPU",
+                       "frames_per_gpu": args.frames, "info_bits_per_gpu_step": bits_per_step,
+                       "l2": "inputs and scratch larger than L2 (no flush needed)",
+                       "waves": mapdec.mapdec_batch_num_waves(b.b),
+                       "parallelism": f"frames sharded, {n_gpus} GPU(s), no collective",
+                       "gen_seconds": round(gen_s, 1)},
+            "roofline": roofline,
+            "algorithmic_tflops": total_alg / (ms / 1e3) / 1e12,
+            "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+    b.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

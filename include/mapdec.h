@@ -132,7 +132,8 @@ typedef struct {
 enum {
     MAPDEC_BATCH_GRAPH = 1,  /* capture the launch sequence in a CUDA graph */
     MAPDEC_BATCH_PLAIN = 2,  /* one frame per launch, default tile sizes, no graph */
-    MAPDEC_BATCH_GRAD = 4    /* allocate for mapdec_batch_loglik_grad */
+    MAPDEC_BATCH_GRAD = 4,   /* allocate for mapdec_batch_loglik_grad */
+    MAPDEC_BATCH_TIMING = 8  /* record CUDA events at phase boundaries of every run */
 };
 
 typedef struct mapdec_batch mapdec_batch_t;
@@ -166,8 +167,8 @@ int mapdec_batch_buffers(mapdec_batch_t *b, uint8_t **rx_dev, float **priors_dev
 
 /*
  * Byte offset of frame f's bits inside the resident rx buffer returned by
- * mapdec_batch_buffers (frames are padded to 16 bytes there); -1 if f is out
- * of range.  Priors and APPs use the sym_offsets of mapdec_batch_layout.
+ * mapdec_batch_buffers (the same dense concatenation as mapdec_batch_layout's
+ * rx_offsets); -1 if f is out of range.
  */
 int64_t mapdec_batch_rx_offset(mapdec_batch_t *b, int frame);
 
@@ -210,6 +211,17 @@ void mapdec_batch_destroy(mapdec_batch_t *b);
  * launches).  For accounting in benchmarks.
  */
 int64_t mapdec_batch_last_launches(mapdec_batch_t *b);
+
+/*
+ * Device time of each phase of the last run, summed over waves (batch created
+ * with MAPDEC_BATCH_TIMING; synchronises the stream).  ms[0..4] = received-bit
+ * packing, forward producers (lattice + W), forward/backward chains, backward
+ * producers (lattice + APP sums), finalize.
+ */
+int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms);
+
+/* Number of waves the batch's frames were split into (scratch budget). */
+int mapdec_batch_num_waves(mapdec_batch_t *b);
 
 #ifdef __cplusplus
 }

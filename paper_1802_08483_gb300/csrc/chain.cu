@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
         if (!(aN > 0.f)) {
             atomicMax(f.status, ST_ZERO);
         } else {
-            *f.loglik = logsum + log((double)aN);
+            *f.loglik = logsum + log((double)aN) - (double)rho * f.logk;
         }
     }
 }
@@ -234,8 +234,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
     const long long P2 = (long long)f.P * f.nsub;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
-    const double Pt = f.dPt, Ps = f.dPs, Pd = f.dPd;
-    const double Qm = Pt * (1.0 - Ps), Qs = Pt * Ps;
+    const double Pt = f.dPt, Ps = f.dPs, Pd = f.dPd, k = f.kappa;
+    // the lattice ran with w' = k Pi/2, Q'm = k Pt (1-Ps), Q's = k Pt Ps
+    const double Qm = k * Pt * (1.0 - Ps), Qs = k * Pt * Ps;
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     bool bad = false;
     for (int i = warp; i < N; i += nw) {
@@ -276,11 +277,14 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
                 Sd += gp[1];
                 Ss += gp[2];
             }
-            // Euler: Pd dR/dPd + Qm dR/dQm + Qs dR/dQs = n R  (R homogeneous of degree n)
+            // Sw, Sd, Ss: sums with dR~/dw', dR~/dPd, dR~/dQ's.  R~ is homogeneous of
+            // degree n in (Pd, Q'm, Q's) (every bit is deleted or transmitted), so
+            // Pd dR~/dPd + Q'm dR~/dQ'm + Q's dR~/dQ's = n R~ gives the Q'm sum.
+            // Chain rule with w' = k Pi/2, Q'm = k Pt (1-Ps), Q's = k Pt Ps, Pt = 1-Pi-Pd.
             const double Sm = ((double)n * z - Pd * Sd - Qs * Ss) / Qm;
-            g0 += (0.5 * Sw - (1.0 - Ps) * Sm - Ps * Ss) * iz;
-            g1 += (Sd - (1.0 - Ps) * Sm - Ps * Ss) * iz;
-            g2 += (-Pt * Sm + Pt * Ss) * iz;
+            g0 += (0.5 * k * Sw - k * (1.0 - Ps) * Sm - k * Ps * Ss) * iz;
+            g1 += (Sd - k * (1.0 - Ps) * Sm - k * Ps * Ss) * iz;
+            g2 += (-k * Pt * Sm + k * Pt * Ss) * iz;
         }
     }
     if (bad && lane == 0) atomicMax(f.status, ST_ZERO);

@@ -103,6 +103,7 @@ int pack_codebook(const uint8_t *cb, int q, int n, std::vector<uint32_t> &out) {
 // ---------------------------------------------------------------------------
 // planning
 // ---------------------------------------------------------------------------
+constexpr int kPhases = 5;  // pack, forward producers, chains, backward producers, finalize
 constexpr size_t kFwdSmemBudget = 110 * 1024;
 constexpr size_t kBwdSmemBudget = 200 * 1024;
 constexpr size_t kChainSmemBudget = 96 * 1024;
@@ -129,16 +130,20 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     f.rho = d.rx_len;
     f.wblk = (long long)rup((size_t)f.M * f.MNS, 4);
     const double Pt = 1.0 - d.Pi - d.Pd;
+    const double kappa = 2.0;        // weight per received bit (see FrameDev)
+    const double w1 = kappa * 0.5 * d.Pi;
     double wp = 1.0;
     for (int a = 0; a <= kMaxI; ++a) {
         f.wpow[a] = (a <= d.I) ? (float)wp : 0.f;
-        f.wder[a] = (a >= 1 && a <= d.I) ? (float)(a * std::pow(0.5 * d.Pi, a - 1)) : 0.f;
-        wp *= 0.5 * d.Pi;
+        f.wder[a] = (a >= 1 && a <= d.I) ? (float)(a * std::pow(w1, a - 1)) : 0.f;
+        wp *= w1;
     }
     f.Pd = (float)d.Pd;
-    f.qsame = (float)(Pt * (1.0 - d.Ps));
-    f.qdiff = (float)(Pt * d.Ps);
+    f.qsame = (float)(kappa * Pt * (1.0 - d.Ps));
+    f.qdiff = (float)(kappa * Pt * d.Ps);
     f.dPi = d.Pi; f.dPd = d.Pd; f.dPs = d.Ps; f.dPt = Pt;
+    f.kappa = kappa;
+    f.logk = std::log(kappa);
 
     auto symbols_span = [&](long long Ppos) -> int {
         return (int)((Ppos - 1 + 2LL * d.xmax) / d.n + 2);
@@ -182,6 +187,14 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     if (!chain_fits(CD)) {
         CD = 1024;
         while (CD > 32 && !chain_fits(CD)) CD /= 2;
+    }
+    if (const char *e = std::getenv("MAPDEC_CHAIN_CD")) {  // tuning / testing override
+        const int cd = std::atoi(e);
+        if (cd >= 32) {
+            FrameDev t = f;
+            t.chainCD = std::min(cd, f.M);
+            if (chain_smem_bytes(t) <= 227 * 1024) CD = t.chainCD;
+        }
     }
     f.chainCD = CD;
 }
@@ -244,10 +257,13 @@ struct mapdec_batch {
     std::vector<Wave> waves;
     std::vector<void *> allocs;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
     cudaGraphExec_t gexec = nullptr;
     bool graph_grad = false;
     int64_t last_launches = 0;
     int64_t launches_per_run[2] = {0, 0};
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // per wave: kPhases + 1 boundaries
 
     void *dalloc(size_t bytes) {
         void *p = nullptr;
@@ -257,6 +273,8 @@ struct mapdec_batch {
     }
     ~mapdec_batch() {
         if (gexec) cudaGraphExecDestroy(gexec);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void *p : allocs) cudaFree(p);
     }
 };
@@ -301,7 +319,7 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         h.scratch_floats = frame_scratch_floats(h.dev, b->grad);
         h.cost = frame_cost(h.dev);
         h.rx_off = b->rx_total;
-        b->rx_total += rup(h.d.rx_len, 16);
+        b->rx_total += h.d.rx_len;  // dense: the caller's concatenation, one copy
         h.sym_off = b->prior_total;  // element offset
         b->prior_total += (int64_t)h.d.N * h.d.q;
         h.rxw_off = b->rxw_total;
@@ -433,30 +451,49 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             w.cls.push_back(c);
         }
     }
+    if (flags & MAPDEC_BATCH_TIMING) {
+        b->timing = true;
+        b->events.resize(b->waves.size() * (kPhases + 1));
+        for (auto &e : b->events) CK(cudaEventCreate(&e));
+    }
     return MAPDEC_OK;
 }
 
-// Enqueue one full run on b->stream.  Throws CudaErr.
-int64_t enqueue_run(mapdec_batch *b, bool grad) {
-    cudaStream_t st = b->stream;
+// Enqueue one full run on stream st.  With timing enabled an event is recorded
+// at every phase boundary (inside a captured graph as external event nodes).
+// Throws CudaErr.
+int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
     int64_t launches = 0;
     CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->nframes * 4, st));
+    int wi = 0;
+    auto mark = [&](int ph) {
+        if (b->timing)
+            CK(cudaEventRecordWithFlags(b->events[(size_t)wi * (kPhases + 1) + ph], st,
+                                        cudaEventRecordExternal));
+    };
     for (auto &w : b->waves) {
         const int nw = w.f1 - w.f0;
+        mark(0);
         CK(launch_pack(w.d_frames, w.d_rxptr, w.d_rxwptr, nw, w.max_words, st));
         ++launches;
+        mark(1);
         for (auto &c : w.cls) {
             CK(launch_fwd(c.n, c.I, w.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
             ++launches;
         }
+        mark(2);
         CK(launch_chain(w.d_frames, w.d_chain, w.nchain, w.smem_chain, st));
         ++launches;
+        mark(3);
         for (auto &c : w.cls) {
             CK(launch_bwd(c.n, c.I, grad, w.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
             ++launches;
         }
+        mark(4);
         CK(launch_finalize(w.d_frames, nw, grad ? 1 : 0, st));
         ++launches;
+        mark(5);
+        ++wi;
     }
     return launches;
 }
@@ -465,22 +502,24 @@ int run_batch(mapdec_batch *b, bool grad) {
     if (grad && !b->grad) return MAPDEC_ERR_ARG;
     const bool use_graph = (b->flags & MAPDEC_BATCH_GRAPH) && !(b->flags & MAPDEC_BATCH_PLAIN);
     if (!use_graph) {
-        b->last_launches = enqueue_run(b, grad);
+        b->last_launches = enqueue_run(b, grad, b->stream);
         return MAPDEC_OK;
     }
     if (!b->gexec || b->graph_grad != grad) {
         if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        // the legacy default stream cannot be captured: capture on a private stream
+        if (!b->cap_stream) CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
         int64_t l = 0;
         try {
-            l = enqueue_run(b, grad);
+            l = enqueue_run(b, grad, b->cap_stream);
         } catch (CudaErr &e) {
-            cudaStreamEndCapture(b->stream, &g);
+            cudaStreamEndCapture(b->cap_stream, &g);
             if (g) cudaGraphDestroy(g);
             throw;
         }
-        CK(cudaStreamEndCapture(b->stream, &g));
+        CK(cudaStreamEndCapture(b->cap_stream, &g));
         cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
         cudaGraphDestroy(g);
         CK(e);
@@ -504,16 +543,7 @@ int worst_status(mapdec_batch *b) {
 // Copy inputs (host or device) into the resident buffers.
 void load_inputs(mapdec_batch *b, const uint8_t *rx_all, const float *priors_all) {
     cudaStream_t st = b->stream;
-    if (rx_all) {
-        // caller buffer is densely concatenated (no padding); resident buffer is padded
-        int64_t src = 0;
-        const bool dev = is_device_ptr(rx_all);
-        for (auto &h : b->fr) {
-            CK(cudaMemcpyAsync(b->d_rx + h.rx_off, rx_all + src, h.d.rx_len,
-                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-            src += h.d.rx_len;
-        }
-    }
+    if (rx_all) copy_in(b->d_rx, rx_all, (size_t)b->rx_total, st);
     if (priors_all) {
         copy_in(b->d_priors, priors_all, (size_t)b->prior_total * 4, st);
     } else {
@@ -595,8 +625,6 @@ int mapdec_batch_layout(mapdec_batch_t *b, int64_t *rx_offsets, int64_t *sym_off
 int mapdec_batch_buffers(mapdec_batch_t *b, uint8_t **rx_dev, float **priors_dev, float **app_dev,
                          double **loglik_dev) {
     if (!b) return MAPDEC_ERR_ARG;
-    // The resident rx buffer pads every frame to 16 bytes; callers filling it in
-    // place must use mapdec_batch_rx_offset.
     if (rx_dev) *rx_dev = b->d_rx;
     if (priors_dev) *priors_dev = b->d_priors;
     if (app_dev) *app_dev = b->d_app;
@@ -682,6 +710,29 @@ int mapdec_batch_set_stream(mapdec_batch_t *b, void *s) {
 void mapdec_batch_destroy(mapdec_batch_t *b) { delete b; }
 
 int64_t mapdec_batch_last_launches(mapdec_batch_t *b) { return b ? b->last_launches : -1; }
+
+int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms) {
+    if (!b || !ms) return MAPDEC_ERR_ARG;
+    if (!b->timing) return MAPDEC_ERR_ARG;
+    for (int k = 0; k < kPhases; ++k) ms[k] = 0.0;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return MAPDEC_ERR_CUDA;
+    }
+    for (size_t w = 0; w < b->waves.size(); ++w)
+        for (int k = 0; k < kPhases; ++k) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, b->events[w * (kPhases + 1) + k],
+                                     b->events[w * (kPhases + 1) + k + 1]) != cudaSuccess) {
+                cudaGetLastError();
+                return MAPDEC_ERR_CUDA;
+            }
+            ms[k] += t;
+        }
+    return MAPDEC_OK;
+}
+
+int mapdec_batch_num_waves(mapdec_batch_t *b) { return b ? (int)b->waves.size() : -1; }
 
 // ---------------------------------------------------------------------------
 // single-frame handle

@@ -40,12 +40,17 @@ struct FrameDev {
     int chainCD;  // destination/source states per chain chunk
     long long rho;
     long long wblk;  // floats per symbol block of W (M * MNS rounded up to 4)
-    // FP32 lattice constants
-    float wpow[kMaxI + 1];   // (Pi/2)^a
-    float wder[kMaxI + 1];   // a (Pi/2)^(a-1)  (d/dw of wpow)
-    float Pd, qsame, qdiff;  // Pd, Pt (1-Ps), Pt Ps
-    // FP64 channel values for the gradient combination
+    // FP32 lattice constants.  Every received bit carries a weight kappa: the
+    // lattice runs with w' = kappa Pi/2 and Q' = kappa Q, so it yields
+    // R~(y|x) = kappa^|y| R(y|x) exactly (kappa is a power of two).  The factor
+    // is common to every term of a symbol's APP sum and shifts log P(Y) by
+    // rho log kappa; it keeps FP32 forward/backward rows within range.
+    float wpow[kMaxI + 1];   // w'^a
+    float wder[kMaxI + 1];   // a w'^(a-1)  (d/dw' of wpow)
+    float Pd, qsame, qdiff;  // Pd, kappa Pt (1-Ps), kappa Pt Ps
+    // FP64 channel values for the log-likelihood and the gradient combination
     double dPi, dPd, dPs, dPt;
+    double kappa, logk;      // received-bit weight and its log
     // inputs
     const uint32_t *rxbits;  // rho bits, bit b of word w = rx[32 w + b]; padded
     const uint32_t *cw;      // q codewords, bit r = x_{r+1}

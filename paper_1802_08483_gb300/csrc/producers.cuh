@@ -407,7 +407,9 @@ __global__ void __launch_bounds__(kThreads) k_rmetric(const FrameDev *__restrict
     float v[kMaxMN];
     eval_metric<NB, IB, 0>(f, p, D, v);
     float *dst = f.Rout + idx * MN;
-    for (int j = 0; j < MN; ++j) dst[j] = v[j];
+    // undo the received-bit weight kappa^j (a power of two: exact)
+    const int lk = (int)lrint(f.logk / 0.6931471805599453);
+    for (int j = 0; j < MN; ++j) dst[j] = ldexpf(v[j], -lk * j);
 }
 
 }  // namespace mdk

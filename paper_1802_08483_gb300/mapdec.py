@@ -31,6 +31,8 @@ MAPDEC_ERR_UNSUPPORTED = 7
 MAPDEC_BATCH_GRAPH = 1
 MAPDEC_BATCH_PLAIN = 2
 MAPDEC_BATCH_GRAD = 4
+MAPDEC_BATCH_TIMING = 8
+PHASES = ("pack", "forward", "chains", "backward", "finalize")
 
 
 class MapDecError(RuntimeError):
@@ -73,6 +75,8 @@ _SIGS = {
     "mapdec_batch_set_stream": (ctypes.c_int, [_VP, _VP]),
     "mapdec_batch_destroy": (None, [_VP]),
     "mapdec_batch_last_launches": (ctypes.c_int64, [_VP]),
+    "mapdec_batch_phase_ms": (ctypes.c_int, [_VP, _VP]),
+    "mapdec_batch_num_waves": (ctypes.c_int, [_VP]),
 }
 
 
@@ -234,6 +238,16 @@ def mapdec_batch_destroy(b):
 
 def mapdec_batch_last_launches(b):
     return int(load().mapdec_batch_last_launches(b))
+
+
+def mapdec_batch_phase_ms(b):
+    ms = np.zeros(5, np.float64)
+    _check(load().mapdec_batch_phase_ms(b, _ptr(ms)), "mapdec_batch_phase_ms")
+    return ms
+
+
+def mapdec_batch_num_waves(b):
+    return int(load().mapdec_batch_num_waves(b))
 
 
 # --------------------------------------------------------------------------
