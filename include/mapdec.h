@@ -60,7 +60,8 @@ enum {
     MAPDEC_ERR_NOMEM = 4,       /* device or host allocation failed */
     MAPDEC_ERR_CUDA = 5,        /* CUDA runtime error or no usable device */
     MAPDEC_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
-    MAPDEC_ERR_UNSUPPORTED = 7  /* parameters outside what the kernels support */
+    MAPDEC_ERR_UNSUPPORTED = 7, /* parameters outside what the kernels support */
+    MAPDEC_ERR_TOO_LARGE = 8    /* frame's scratch exceeds mapdec_decode_noalloc's arena */
 };
 
 typedef struct mapdec mapdec_t;
@@ -113,6 +114,7 @@ int mapdec_receiver_metric(mapdec_t *h, const uint8_t *rx, int64_t rx_len, float
 /* Release a handle and its device scratch (NULL is ignored). */
 void mapdec_destroy(mapdec_t *h);
 
+
 /* Static string for a status code. */
 const char *mapdec_strerror(int status);
 
@@ -127,6 +129,34 @@ typedef struct {
     const uint8_t *codebook; /* q*n bytes, host or device; copied at create */
     int64_t rx_len;          /* rho of this frame */
 } mapdec_frame_desc_t;
+
+/*
+ * Decode one frame without allocating any memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate once
+ * running -- a receive pipeline whose memory is fixed at start-up, a host
+ * framework that owns every device allocation, real-time code that must not
+ * risk a cudaMalloc blocking, fragmenting or failing mid-stream.
+ *   frame: code, channel, drift limit and rx_len of the frame; its codebook
+ *     (q*n bytes) may be host or device memory.  q <= 64.
+ *   rx_dev (rx_len bytes), priors_dev (N*q floats, or NULL for uniform 1/q),
+ *   app_dev (N*q floats), loglik_dev (1 double): device memory owned by the
+ *   caller.
+ *   cuda_stream: a cudaStream_t (NULL = default stream).
+ * Results equal mapdec_decode's.  All scratch lives in one static device
+ * array of 32 MiB per GPU that loads the library, held until the process
+ * exits; a frame whose scratch does not fit is rejected with
+ * MAPDEC_ERR_TOO_LARGE (about N * (2 xmax + 1) * (n(I+1)+1) * 4 bytes for the
+ * transition sums dominates).  The first call on a device looks up the
+ * array's address on that device; make that first call before any stream
+ * capture.  Every call shares the array and leaves its contents behind (the
+ * next call clears what must start at zero), so calls whose work overlaps on
+ * the GPU -- concurrent streams, threads or devices sharing a context -- race
+ * and must be serialised by the caller.  The call returns after the stream
+ * has drained, with the decode's status.
+ */
+int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_dev,
+                          const float *priors_dev, float *app_dev, double *loglik_dev,
+                          void *cuda_stream);
 
 /* batch flags */
 enum {

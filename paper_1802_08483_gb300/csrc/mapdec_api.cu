@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <set>
 #include <string>
 #include <vector>
@@ -559,6 +560,98 @@ void load_inputs(mapdec_batch *b, const uint8_t *rx_all, const float *priors_all
 
 }  // namespace
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free decode of one frame.
+//
+// Some callers cannot allocate device memory once they are running: a
+// receiver pipeline whose memory is fixed at start-up, a host framework that
+// owns every device allocation itself, or real-time code that must not risk a
+// cudaMalloc blocking, fragmenting or failing in mid-stream.  For them the
+// whole scratch of one decode (descriptor, work lists, packed bits, W, alpha,
+// beta, APP partial sums, status) is carved out of the file-scope array
+// below, which every GPU that loads the library holds until the process
+// exits.  Nothing is allocated per call, on the device or on the host.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB
+constexpr int kStaticMaxQ = 64;
+constexpr int kStaticMaxDevices = 64;
+
+struct StaticCodebook {
+    uint32_t w[kStaticMaxQ];
+};
+
+std::mutex g_static_mu;
+void *g_static_addr[kStaticMaxDevices] = {};
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+// Device address of the static arena on the current device.  The host-side
+// name g_static_scratch is only a stand-in; the address is looked up once per
+// device with that device current.
+int static_scratch_address(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return MAPDEC_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kStaticMaxDevices) return MAPDEC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return MAPDEC_ERR_CUDA;
+        }
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return MAPDEC_OK;
+}
+
+// Writes the descriptor, work lists and pointer tables into the arena, fills
+// uniform priors if none were given, and clears the status word (the arena
+// keeps the previous call's contents).
+__global__ void k_static_setup(FrameDev f, FrameDev *fdst, Work *fwd, int T, Work *bwd, int T2,
+                               Work *chain, const uint8_t **rxp, uint32_t **rxwp,
+                               const uint8_t *rx, uint32_t *rxw, uint32_t *cwdst,
+                               StaticCodebook cb, int q, float *uni, long long nuni,
+                               float uval, int *status) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long t = tid; t < T; t += nth) fwd[t] = Work{0, (int)t};
+    for (long long t = tid; t < T2; t += nth) bwd[t] = Work{0, (int)t};
+    for (long long k = tid; k < nuni; k += nth) uni[k] = uval;
+    for (long long d = tid; d < q; d += nth) cwdst[d] = cb.w[d];
+    if (tid == 0) {
+        *fdst = f;
+        chain[0] = Work{0, 0};
+        chain[1] = Work{0, 1};
+        rxp[0] = rx;
+        rxwp[0] = rxw;
+        *status = 0;
+    }
+}
+
+bool device_pointer(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -574,6 +667,7 @@ const char *mapdec_strerror(int s) {
         case MAPDEC_ERR_CUDA: return "CUDA error or no usable device";
         case MAPDEC_ERR_TIMEOUT: return "device-side wait timed out";
         case MAPDEC_ERR_UNSUPPORTED: return "parameters outside the supported range";
+        case MAPDEC_ERR_TOO_LARGE: return "frame needs more scratch than the static arena of mapdec_decode_noalloc holds";
         default: return "unknown status";
     }
 }
@@ -842,5 +936,116 @@ int mapdec_receiver_metric(mapdec_t *h, const uint8_t *rx, int64_t rx_len, float
 }
 
 void mapdec_destroy(mapdec_t *h) { delete h; }
+
+int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_dev,
+                          const float *priors_dev, float *app_dev, double *loglik_dev,
+                          void *cuda_stream) {
+    if (!frame || !app_dev || !loglik_dev) return MAPDEC_ERR_ARG;
+    const mapdec_frame_desc_t &d = *frame;
+    int st = validate(d.q, d.n, d.N, d.Pi, d.Pd, d.Ps, d.I, d.xmax);
+    if (st) return st;
+    if (d.q > kStaticMaxQ) return MAPDEC_ERR_TOO_LARGE;
+    const long long tau = (long long)d.n * d.N;
+    if (d.rx_len < 0) return MAPDEC_ERR_ARG;
+    if (std::llabs(d.rx_len - tau) > d.xmax) return MAPDEC_ERR_DRIFT_RANGE;
+    if ((d.rx_len > 0 && !device_pointer(rx_dev)) || !device_pointer(app_dev) ||
+        !device_pointer(loglik_dev) || (priors_dev && !device_pointer(priors_dev)))
+        return MAPDEC_ERR_ARG;
+    // codebook: host or device bytes, copied into a stack buffer and packed
+    if (!d.codebook) return MAPDEC_ERR_ARG;
+    uint8_t cbytes[kStaticMaxQ * 31];
+    const size_t cbn = (size_t)d.q * d.n;
+    if (device_pointer(d.codebook)) {
+        if (cudaMemcpy(cbytes, d.codebook, cbn, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return MAPDEC_ERR_CUDA;
+        }
+    } else {
+        std::memcpy(cbytes, d.codebook, cbn);
+    }
+    StaticCodebook cb;
+    for (int k = 0; k < d.q; ++k) {
+        uint32_t w = 0;
+        for (int r = 0; r < d.n; ++r) {
+            const uint8_t bit = cbytes[(size_t)k * d.n + r];
+            if (bit > 1) return MAPDEC_ERR_ARG;
+            if (bit) w |= (1u << r);
+        }
+        for (int k2 = 0; k2 < k; ++k2)
+            if (cb.w[k2] == w) return MAPDEC_ERR_ARG;  // the encoding must be injective
+        cb.w[k] = w;
+    }
+    void *base = nullptr;
+    st = static_scratch_address(&base);
+    if (st) return st;
+
+    FrameDev f{};
+    plan_shape(f, d, false, 0);
+    // carve the arena (every region 256-byte aligned)
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> size_t {
+        const size_t o = off;
+        off += rup(bytes, 256);
+        return o;
+    };
+    const size_t o_frame = take(sizeof(FrameDev));
+    const size_t o_fwd = take(sizeof(Work) * (size_t)f.T);
+    const size_t o_bwd = take(sizeof(Work) * (size_t)f.T2);
+    const size_t o_chain = take(sizeof(Work) * 2);
+    const size_t o_rxp = take(sizeof(void *));
+    const size_t o_rxwp = take(sizeof(void *));
+    const long long nwords = (d.rx_len + 31) / 32 + 4;
+    const size_t o_rxw = take(4 * (size_t)nwords);
+    const size_t o_cw = take(4 * (size_t)d.q);
+    const size_t o_pri = priors_dev ? off : take(4 * (size_t)d.N * d.q);
+    const size_t o_W = take(4 * ((size_t)f.N * f.wblk + 16));
+    const size_t o_a = take(4 * (size_t)(f.N + 1) * f.Mp);
+    const size_t o_b = take(4 * (size_t)(f.N + 1) * f.Mp);
+    const size_t o_Lp = take(4 * (size_t)f.T2 * f.S2 * f.q);
+    const size_t o_st = take(sizeof(int));
+    if (off > kStaticScratchBytes) return MAPDEC_ERR_TOO_LARGE;
+
+    unsigned char *A = (unsigned char *)base;
+    f.rxbits = (const uint32_t *)(A + o_rxw);
+    f.cw = (const uint32_t *)(A + o_cw);
+    f.priors = priors_dev ? priors_dev : (const float *)(A + o_pri);
+    f.W = (float *)(A + o_W);
+    f.alpha = (float *)(A + o_a);
+    f.beta = (float *)(A + o_b);
+    f.Lp = (float *)(A + o_Lp);
+    f.Gp = nullptr;
+    f.Rout = nullptr;
+    f.app = app_dev;
+    f.dpriors = nullptr;
+    f.loglik = loglik_dev;
+    f.dchan = nullptr;
+    f.status = (int *)(A + o_st);
+
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    FrameDev *fdev = (FrameDev *)(A + o_frame);
+    Work *wf = (Work *)(A + o_fwd), *wb = (Work *)(A + o_bwd), *wc = (Work *)(A + o_chain);
+    const long long nuni = priors_dev ? 0 : (long long)d.N * d.q;
+    k_static_setup<<<64, 256, 0, s>>>(f, fdev, wf, f.T, wb, f.T2, wc,
+                                      (const uint8_t **)(A + o_rxp), (uint32_t **)(A + o_rxwp),
+                                      rx_dev, (uint32_t *)(A + o_rxw), (uint32_t *)(A + o_cw), cb,
+                                      d.q, (float *)(A + o_pri), nuni, 1.0f / (float)d.q,
+                                      f.status);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_pack(fdev, (const uint8_t *const *)(A + o_rxp), (uint32_t *const *)(A + o_rxwp), 1,
+                        nwords, s);
+    if (e == cudaSuccess) e = launch_fwd(d.n, d.I, fdev, wf, f.T, fwd_smem_bytes(f), s);
+    if (e == cudaSuccess) e = launch_chain(fdev, wc, 2, chain_smem_bytes(f), s);
+    if (e == cudaSuccess) e = launch_bwd(d.n, d.I, false, fdev, wb, f.T2, bwd_smem_bytes(f, false), s);
+    if (e == cudaSuccess) e = launch_finalize(fdev, 1, 0, s);
+    int status = MAPDEC_OK;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, f.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return map_cuda(e);
+    }
+    return status;
+}
 
 }  // extern "C"

@@ -27,6 +27,7 @@ MAPDEC_ERR_NOMEM = 4
 MAPDEC_ERR_CUDA = 5
 MAPDEC_ERR_TIMEOUT = 6
 MAPDEC_ERR_UNSUPPORTED = 7
+MAPDEC_ERR_TOO_LARGE = 8
 
 MAPDEC_BATCH_GRAPH = 1
 MAPDEC_BATCH_PLAIN = 2
@@ -61,6 +62,7 @@ _SIGS = {
     "mapdec_loglik_grad": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
     "mapdec_receiver_metric": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
     "mapdec_destroy": (None, [_VP]),
+    "mapdec_decode_noalloc": (ctypes.c_int, [ctypes.POINTER(FrameDesc), _VP, _VP, _VP, _VP, _VP]),
     "mapdec_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mapdec_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(FrameDesc),
                                            ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
@@ -164,6 +166,16 @@ def mapdec_receiver_metric(h, rx, rx_len, R_out):
 
 def mapdec_destroy(h):
     load().mapdec_destroy(h)
+
+
+def mapdec_decode_noalloc(frame, rx_dev, priors_dev, app_dev, loglik_dev, stream=None):
+    """frame: object with q, n, N, I, xmax, Pi, Pd, Ps, codebook and rho (or rx_len)."""
+    cb = np.ascontiguousarray(frame.codebook, dtype=np.uint8)
+    rho = frame.rho if hasattr(frame, "rho") else int(frame.rx_len)
+    desc = FrameDesc(int(frame.q), int(frame.n), int(frame.N), int(frame.I), int(frame.xmax),
+                     float(frame.Pi), float(frame.Pd), float(frame.Ps), cb.ctypes.data, int(rho))
+    return load().mapdec_decode_noalloc(ctypes.byref(desc), _ptr(rx_dev), _ptr(priors_dev),
+                                        _ptr(app_dev), _ptr(loglik_dev), stream)
 
 
 def mapdec_batch_create(frames, flags=0, mem_budget_bytes=0):
