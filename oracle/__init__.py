@@ -76,6 +76,8 @@ def _load():
         lib.orc_forward_backward.restype = ctypes.c_int
         lib.orc_loglik_grad.argtypes = common + [ctypes.c_int, dp, dp, dp]
         lib.orc_loglik_grad.restype = ctypes.c_int
+        lib.orc_set_received_bit_weight.argtypes = [ctypes.c_double]
+        lib.orc_set_received_bit_weight.restype = None
         _lib = lib
         return lib
 
@@ -125,9 +127,12 @@ def _frame_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors):
     return q, n, args, keep
 
 
-def decode(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True):
-    """APPs (N, q) and log P(Y) of one frame (FP64)."""
+def decode(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True, kappa=1.0):
+    """APPs (N, q) and log P(Y) of one frame (FP64).  kappa != 1 applies the
+    exact received-bit reweighting (for frames whose literal recursion
+    underflows FP64)."""
     lib = _load()
+    lib.orc_set_received_bit_weight(float(kappa))
     q, n, args, keep = _frame_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
     app = np.zeros((N, q), np.float64)
     ll = ctypes.c_double(0.0)
@@ -138,9 +143,10 @@ def decode(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True):
     return app, ll.value
 
 
-def loglik(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True) -> float:
+def loglik(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True, kappa=1.0) -> float:
     """log P(Y) only (forward pass)."""
     lib = _load()
+    lib.orc_set_received_bit_weight(float(kappa))
     q, n, args, keep = _frame_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
     ll = ctypes.c_double(0.0)
     st = lib.orc_decode(*args, int(bool(memo)), _NULL_D, ctypes.byref(ll))
@@ -150,8 +156,9 @@ def loglik(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True) -> floa
 
 
 def forward_backward(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None):
-    """Normalised alpha, beta ((N+1, M) each) and log c_1..log c_N."""
+    """Normalised alpha, beta ((N+1, M) each) and log c_1..log c_N (literal)."""
     lib = _load()
+    lib.orc_set_received_bit_weight(1.0)
     q, n, args, keep = _frame_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
     M = 2 * xmax + 1
     A = np.zeros((N + 1, M), np.float64)
@@ -166,9 +173,10 @@ def forward_backward(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None):
 
 
 def loglik_grad(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True,
-                want_chan=True, want_priors=True):
+                want_chan=True, want_priors=True, kappa=1.0):
     """(logP, d logP/d(Pi,Pd,Ps) or None, d logP/d priors (N,q) or None)."""
     lib = _load()
+    lib.orc_set_received_bit_weight(float(kappa))
     q, n, args, keep = _frame_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
     dpp = ctypes.POINTER(ctypes.c_double)
     dchan = np.zeros(3, np.float64) if want_chan else None
@@ -183,7 +191,7 @@ def loglik_grad(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True,
     return ll.value, dchan, dpri
 
 
-def decode_frame(fr, memo=True):
+def decode_frame(fr, memo=True, kappa=1.0):
     """Convenience: decode a synthetic frame object (fields as in the input generator)."""
     return decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
-                  priors=fr.priors, memo=memo)
+                  priors=fr.priors, memo=memo, kappa=kappa)

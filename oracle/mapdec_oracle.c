@@ -40,6 +40,17 @@
  * The optional memo caches R(.|C(D)) per (rx start p, D): the same lattice
  * function evaluated once per key, so results are bitwise identical to the
  * un-memoised (i, m', D) grid; it only saves time on large frames.
+ *
+ * Optional received-bit weight kappa (default 1: the literal recursion).  The
+ * normalised forward row alpha_i(m) is the probability of a received prefix of
+ * n i + m bits, so its entries fall off by roughly 2^-h per bit of drift (h the
+ * entropy rate of the received bits).  On long frames with wide drift limits
+ * the entries that carry the posterior fall below even the FP64 range and the
+ * literal recursion reports a zero-probability frame.  With kappa != 1 every
+ * gamma is multiplied by kappa^(received length), which multiplies every path
+ * of the frame by the same kappa^rho: APPs are unchanged, log P(Y) is recovered
+ * by subtracting rho log kappa, and the rows stay representable.  The tests
+ * check that results agree with kappa = 1 wherever the literal recursion works.
  */
 #include <math.h>
 #include <stdint.h>
@@ -188,6 +199,11 @@ static int orc_receiver_metric_dual(int n, int I, const uint8_t *x, const uint8_
 /* Frame context                                                       */
 /* ------------------------------------------------------------------ */
 
+static double g_kappa = 1.0;
+
+/* Received-bit weight used by the decode entry points (1 = literal). */
+void orc_set_received_bit_weight(double kappa) { g_kappa = (kappa > 0.0) ? kappa : 1.0; }
+
 typedef struct {
     int q, n, N, I, xmax, M, Mn;
     int64_t rho;
@@ -273,11 +289,13 @@ static int orc_gamma(orc_ctx *c, int i, double *g, double *R)
             int st = orc_R(c, p, D, Rj);
             if (st) { free(Rj); return st; }
             const double pr = orc_prior(c, i, D);
+            double kw = 1.0;  /* kappa^k, k = received length */
             for (int k = 0; k < Mn; ++k) {
                 const int m2 = m1 + (k - n);
                 const int inside = (m2 >= -xmax && m2 <= xmax);
-                gd[k] = inside ? pr * Rj[k] : 0.0;
-                if (Rd) Rd[k] = inside ? Rj[k] : 0.0;
+                gd[k] = inside ? pr * Rj[k] * kw : 0.0;
+                if (Rd) Rd[k] = inside ? Rj[k] * kw : 0.0;
+                kw *= g_kappa;
             }
         }
     }
@@ -302,9 +320,11 @@ static int orc_gamma_dual(orc_ctx *c, int i, dual *g)
             int st = orc_R_dual(c, p, D, Rj);
             if (st) { free(Rj); return st; }
             const double pr = orc_prior(c, i, D);
+            double kw = 1.0;
             for (int k = 0; k < Mn; ++k) {
                 const int m2 = m1 + (k - n);
-                gd[k] = (m2 >= -xmax && m2 <= xmax) ? d_scale(Rj[k], pr) : d_const(0.0);
+                gd[k] = (m2 >= -xmax && m2 <= xmax) ? d_scale(Rj[k], pr * kw) : d_const(0.0);
+                kw *= g_kappa;
             }
         }
     }
@@ -496,7 +516,7 @@ int orc_decode(int q, int n, const uint8_t *codebook, int N, double Pi, double P
     if (!st) {
         const double aN = A[(size_t)N * c.M + (int)(rho - (int64_t)n * N) + xmax];
         if (!(aN > 0.0)) st = ORC_ERR_ZERO_PROB;
-        else if (loglik) *loglik = ls + log(aN);
+        else if (loglik) *loglik = ls + log(aN) - (double)rho * log(g_kappa);
     }
     if (!st && app) st = orc_backward(&c, B);
     if (!st && app) st = orc_app(&c, A, B, app, NULL, NULL);
@@ -598,7 +618,7 @@ int orc_loglik_grad(int q, int n, const uint8_t *codebook, int N, double Pi, dou
             else {
                 dual lp = d_add(ls, d_log(a[end]));
                 for (int k = 0; k < 3; ++k) dlogp_dchan[k] = lp.d[k];
-                if (loglik) *loglik = lp.v;
+                if (loglik) *loglik = lp.v - (double)rho * log(g_kappa);
             }
         }
         free(g); free(a); free(an);
@@ -615,7 +635,7 @@ int orc_loglik_grad(int q, int n, const uint8_t *codebook, int N, double Pi, dou
         if (!st && !dlogp_dchan && loglik) {
             const double aN = A[(size_t)N * M + end];
             if (!(aN > 0.0)) st = ORC_ERR_ZERO_PROB;
-            else *loglik = ls + log(aN);
+            else *loglik = ls + log(aN) - (double)rho * log(g_kappa);
         }
         if (!st && dlogp_dpriors) st = orc_backward(&c, B);
         if (!st && dlogp_dpriors) st = orc_app(&c, A, B, NULL, dlogp_dpriors, Z);

@@ -7,8 +7,9 @@
 //                transition sums W_i(s', j) stream from global memory into
 //                shared memory by 1-D bulk copies (cp.async.bulk) completed on
 //                mbarriers, double-buffered, while the previous chunk is used.
-//                The forward chain accumulates sum_i log c_i in FP64 and writes
-//                log P(Y) = sum_i log c_i + log alpha_N(rho - tau).
+//                Rows are kept exponentially tilted (see below) so that FP32
+//                holds them; the forward chain keeps the exact FP64 record of
+//                every normaliser and tilt and writes log P(Y).
 //   k_finalize : APPs (eq. L, normalised over D), d logP / d prior and the
 //                FP64 reduction of the channel-parameter gradient.
 #include "mapdec_dev.cuh"
@@ -55,6 +56,29 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return s;
 }
 
+// Two sums at once (normaliser and first moment).
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) { red[warp] = a; red[32 + warp] = b; }
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < nw; ++w) { sa += red[w]; sb += red[32 + w]; }
+    a = sa;
+    b = sb;
+}
+
+// Tilt controller (see k_chain).
+constexpr double kTiltGainMin = 0.02;  // long-run smoothing of the entropy-rate estimate
+constexpr double kTiltStepMax = 0.02;  // largest change of the tilt between two rows
+constexpr double kTiltMin = 0.2, kTiltMax = 1.6;
+
 // Geometry of chunk k of the step that consumes W_i.
 struct ChunkGeom {
     int d0, d1;     // owned states (alpha: destinations, beta: sources)
@@ -87,6 +111,20 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const FrameDev &f, int dir, int 
     return g;
 }
 
+// Exponential tilt.  The forward metric alpha_i(m) is the joint probability of
+// a received prefix of L = n i + m bits, so a row falls off roughly like
+// 2^{-h L} (h: entropy rate of the received bits) on top of the drift
+// posterior; the backward metric rises the same way.  Far apart in FP32, the
+// entries that carry the posterior would underflow.  The chains therefore store
+//   alpha^_i(m) = alpha_i(m) 2^{theta_i L} / Z_i,   beta^_i(m) = beta_i(m) 2^{-theta'_i L} / Y_i
+// with tilts theta driven toward h by the normalisers: with a tilt theta a
+// step's normaliser is about 2^{(theta - h) n}, so theta_{i+1} = theta_i -
+// g log2(c_i) / n (g = 1/(steps+1), floored at kTiltGainMin).  The producers
+// already weight every received bit by 2 (theta = 1), so a step multiplies the
+// transition sums by 2^{(theta - 1) j} (j = received length) and pre-scales
+// the source row by 2^{(theta_{i+1} - theta_i)(m - mean)}; Z_i and the tilts
+// are kept exactly in FP64, and log P(Y) = log alpha^_N(rho - tau) + log Z_N
+// - theta_N rho log 2.  The APP producer applies the matching exact factor.
 __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restrict__ frames,
                                                          const Work *__restrict__ work) {
     const Work wk = work[blockIdx.x];
@@ -100,7 +138,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
     const int send = (int)(rho - (long long)n * N) + xmax;  // state of the end drift
 
     __shared__ uint64_t bar[kStages];
-    __shared__ double red[32];
+    __shared__ double red[64];
     __shared__ int s_fail;
     extern __shared__ float4 sm4[];
     float *cur = reinterpret_cast<float *>(sm4);
@@ -126,25 +164,77 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
         const int st = (int)(g / nck);
         return dir == 0 ? st : N - 1 - st;
     };
+    // Self-check of every copy: source inside this frame's W, destination inside
+    // its stage, 16-byte alignment and size.  A violation records ST_ARG in the
+    // frame status and completes the stage's phase with a plain arrive instead.
+    const float *wlo = f.W;
+    const float *whi = f.W + (size_t)N * f.wblk + 16;
     auto issue = [&](long long g) {
         const int i = step_symbol(g);
         const int k = (int)(g % nck);
         const ChunkGeom cg = chunk_geom(f, dir, i, k);
         uint64_t *b = &bar[g % kStages];
         float *dst = stage0 + (size_t)(g % kStages) * stageFloats;
-        mbar_expect_tx(b, cg.bytes);
-        bulk_g2s(dst, cg.src, cg.bytes, b);
+        const bool ok = cg.src >= wlo && cg.src + cg.bytes / 4 <= whi &&
+                        cg.bytes % 16 == 0 && cg.bytes / 4 <= stageFloats &&
+                        ((uintptr_t)cg.src & 15) == 0 && ((uintptr_t)dst & 15) == 0;
+        if (ok) {
+            mbar_expect_tx(b, cg.bytes);
+            bulk_g2s(dst, cg.src, cg.bytes, b);
+        } else {
+            atomicMax(f.status, ST_ARG);
+            mbar_arrive(b);
+        }
     };
     if (threadIdx.x == 0)
         for (long long g = 0; g < kStages && g < total; ++g) issue(g);
 
-    double logsum = 0.0;
-    double part = 0.0;  // this thread's share of the current normaliser
+    __shared__ double s_th[3];  // tilt of the current row, of the row being built, row mean
+    __shared__ float vfac[kMaxMN];
+    double logZ = 0.0;       // thread 0: log Z_i (forward) in nats
+    double theta = 1.0;      // thread 0: tilt of the current row
+    double mean = (dir == 0) ? 0.0 : (double)(send - xmax);  // thread 0: mean drift of it
+    double lc_prev = 0.0;    // thread 0: log2 of the last normaliser
+    long long steps = 0;
+    if (threadIdx.x == 0) {
+        if (dir == 0) { f.thf[0] = 1.0; f.mcf[0] = 0.0; }
+        else f.thb[N] = 1.0;
+    }
+    double part = 0.0, partm = 0.0;  // this thread's share of the normaliser and first moment
+    float th_cur = 1.f, th_new = 1.f, mc = 0.f;
     bool failed = false;
     long long gfail = 0;
     for (long long g = 0; g < total; ++g) {
         const int i = step_symbol(g);
         const int k = (int)(g % nck);
+        if (k == 0) {
+            // start of a step: choose the tilt of the row this step produces
+            if (threadIdx.x == 0) {
+                double tn = theta;
+                if (steps > 0) {
+                    const double gain = fmax(kTiltGainMin, 1.0 / (double)(steps + 1));
+                    const double d = fmin(kTiltStepMax, fmax(-kTiltStepMax, -gain * lc_prev / n));
+                    tn = fmin(kTiltMax, fmax(kTiltMin, theta + d));
+                }
+                s_th[0] = theta;
+                s_th[1] = tn;
+                s_th[2] = mean;
+            }
+            __syncthreads();
+            th_cur = (float)s_th[0];
+            th_new = (float)s_th[1];
+            mc = (float)s_th[2];
+            // forward: transition weight 2^{(theta_{i+1}-1) j}; backward: 2^{(theta'_{i+1}-1) j}
+            const float phi = (dir == 0 ? th_new : th_cur) - 1.f;
+            for (int j = threadIdx.x; j < MN; j += blockDim.x) vfac[j] = exp2f(phi * (float)j);
+            if (dir == 0) {
+                const float dth = th_new - th_cur;
+                if (dth != 0.f)
+                    for (int s = threadIdx.x; s < M; s += blockDim.x)
+                        cur[s] *= exp2f(dth * ((float)(s - xmax) - mc));
+            }
+            __syncthreads();
+        }
         const ChunkGeom cg = chunk_geom(f, dir, i, k);
         const float *buf = stage0 + (size_t)(g % kStages) * stageFloats + cg.shift;
         if (!mbar_wait(&bar[g % kStages], (uint32_t)((g / kStages) & 1), kWaitLimit)) {
@@ -161,36 +251,56 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
                 const int jlo = max(0, s + n - hi), jhi = min(MN - 1, s + n - lo);
                 for (int j = jlo; j <= jhi; ++j) {
                     const int src = s - j + n;
-                    acc = fmaf(cur[src], buf[(size_t)(src - cg.r0) * MNS + j], acc);
+                    acc = fmaf(cur[src], buf[(size_t)(src - cg.r0) * MNS + j] * vfac[j], acc);
                 }
                 nxt[s] = acc;
                 part += (double)acc;
+                partm += (double)acc * (double)(s - xmax);
             }
         } else {
+            const float dth = th_cur - th_new;  // post-scale 2^{(theta'_{i+1} - theta'_i)(m - mean)}
             for (int s = cg.d0 + threadIdx.x; s < cg.d1; s += blockDim.x) {
                 float acc = 0.f;
                 if (s >= vlo && s <= vhi) {
                     const int jlo = max(0, n - s), jhi = min(MN - 1, M - 1 - s + n);
                     const float *w = buf + (size_t)(s - cg.r0) * MNS;
-                    for (int j = jlo; j <= jhi; ++j) acc = fmaf(w[j], cur[s + j - n], acc);
+                    for (int j = jlo; j <= jhi; ++j)
+                        acc = fmaf(w[j] * vfac[j], cur[s + j - n], acc);
+                    if (dth != 0.f) acc *= exp2f(dth * ((float)(s - xmax) - mc));
                 }
                 nxt[s] = acc;
                 part += (double)acc;
+                partm += (double)acc * (double)(s - xmax);
             }
         }
         __syncthreads();  // stage consumed by everyone
         if (threadIdx.x == 0 && g + kStages < total) issue(g + kStages);
         if (k == nck - 1) {
-            // end of a step: normalise
-            const double c = block_sum(part, red);
+            // end of a step: normalise, keep the FP64 record
+            double c = part, cm = partm;
+            block_sum2(c, cm, red);
             part = 0.0;
+            partm = 0.0;
             if (!(c > 0.0) || !isfinite(c)) {
                 if (threadIdx.x == 0) atomicCAS(&s_fail, 0, ST_ZERO);
             }
             __syncthreads();
             if (s_fail) { failed = true; gfail = g; break; }
             const float inv = (float)(1.0 / c);
-            if (dir == 0) logsum += log(c);
+            if (threadIdx.x == 0) {
+                const double dth = (double)th_new - (double)th_cur;
+                if (dir == 0) {
+                    logZ += log(c) + dth * ((double)n * i + (double)mc) * 0.6931471805599453;
+                    f.thf[i + 1] = (double)th_new;
+                    f.mcf[i + 1] = cm / c;
+                } else {
+                    f.thb[i] = (double)th_new;
+                }
+                theta = (double)th_new;
+                mean = cm / c;
+                lc_prev = log2(c);
+                ++steps;
+            }
             float *row = (dir == 0) ? f.alpha + (size_t)(i + 1) * Mp : f.beta + (size_t)i * Mp;
             for (int s = threadIdx.x; s < M; s += blockDim.x) {
                 const float v = nxt[s] * inv;
@@ -216,7 +326,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
         if (!(aN > 0.f)) {
             atomicMax(f.status, ST_ZERO);
         } else {
-            *f.loglik = logsum + log((double)aN) - (double)rho * f.logk;
+            *f.loglik = log((double)aN) + logZ - theta * (double)rho * 0.6931471805599453;
         }
     }
 }

@@ -206,6 +206,7 @@ size_t frame_scratch_floats(const FrameDev &f, bool grad) {
     s += rup((size_t)(f.N + 1) * f.Mp, 64) * 2;          // alpha, beta
     s += rup((size_t)f.T2 * f.S2 * f.q, 64);             // Lp
     if (grad) s += rup((size_t)f.T2 * f.S2 * 3, 64);     // Gp
+    s += 3 * rup((size_t)(f.N + 1) * 2, 64);             // thf, mcf, thb (doubles)
     return s;
 }
 
@@ -392,6 +393,9 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             f.Lp = base + o; o += rup((size_t)f.T2 * f.S2 * f.q, 64);
             f.Gp = nullptr;
             if (b->grad) { f.Gp = base + o; o += rup((size_t)f.T2 * f.S2 * 3, 64); }
+            f.thf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+            f.mcf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+            f.thb = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
             off += o;
             f.Rout = nullptr;
             f.app = b->d_app + h.sym_off;
@@ -1002,6 +1006,9 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     const size_t o_a = take(4 * (size_t)(f.N + 1) * f.Mp);
     const size_t o_b = take(4 * (size_t)(f.N + 1) * f.Mp);
     const size_t o_Lp = take(4 * (size_t)f.T2 * f.S2 * f.q);
+    const size_t o_thf = take(8 * (size_t)(f.N + 1));
+    const size_t o_mcf = take(8 * (size_t)(f.N + 1));
+    const size_t o_thb = take(8 * (size_t)(f.N + 1));
     const size_t o_st = take(sizeof(int));
     if (off > kStaticScratchBytes) return MAPDEC_ERR_TOO_LARGE;
 
@@ -1013,6 +1020,9 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     f.alpha = (float *)(A + o_a);
     f.beta = (float *)(A + o_b);
     f.Lp = (float *)(A + o_Lp);
+    f.thf = (double *)(A + o_thf);
+    f.mcf = (double *)(A + o_mcf);
+    f.thb = (double *)(A + o_thb);
     f.Gp = nullptr;
     f.Rout = nullptr;
     f.app = app_dev;

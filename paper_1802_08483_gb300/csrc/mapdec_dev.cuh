@@ -62,6 +62,10 @@ struct FrameDev {
     float *Lp;       // T2 * S2 * q  partial unnormalised APP sums per super-tile
     float *Gp;       // T2 * S2 * 3  partial tangent sums per super-tile (gradient mode)
     float *Rout;     // receiver-metric dump (debug entry), (rho+1)*q*MN or null
+    // Exponential tilt of the stored forward/backward rows (see k_chain):
+    // thf[i], mcf[i]: tilt and mean drift of forward row i; thb[i]: tilt of
+    // backward row i.  N+1 doubles each.
+    double *thf, *mcf, *thb;
     // outputs
     float *app;      // N*q
     float *dpriors;  // N*q or null
@@ -240,6 +244,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // 1-D bulk copy global -> shared, completion counted on `bar`.
 // dst, src 16-byte aligned; bytes a multiple of 16.

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd(const FrameDev *__restrict__ f
 // Per sub-tile this is a GEMM  C (S x NR*DS) = AB (S x K) * Rt (K x NR*DS),
 // K = P*MN, whose A operand AB[c][il] = alpha*beta is built in chunks.
 // smem: Rt[K][CW]  (CW = NR*DS, DS = roundup4(q); column t*DS + D)
-//       Aw[S][P], Bw[S][BW] (BW = P + MN - 1)
+//       Aw[S][P], Bw[S][BW] (BW = P + MN - 1), Vj[S][MN] (tilt factor per j)
 //       AB[kKC][S4] / reduction scratch
 //       Lacc[S2][q], Gacc[S2][3], Ct[3][S4][DS] (gradient mode)
 // ---------------------------------------------------------------------------
@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
     float *Rt = reinterpret_cast<float *>(smem4);
     float *Aw = Rt + (size_t)K * CW;
     float *Bw = Aw + (((size_t)f.S * P + 3) & ~(size_t)3);
-    float *AB = Bw + (((size_t)f.S * BW + 3) & ~(size_t)3);
+    float *Vj = Bw + (((size_t)f.S * BW + 3) & ~(size_t)3);
+    float *AB = Vj + (((size_t)f.S * MN + 3) & ~(size_t)3);
     size_t abn = (size_t)kKC * Smax4;
     if (abn < (size_t)kThreads * 16) abn = (size_t)kThreads * 16;
     float *Lacc = AB + abn;
@@ -240,18 +241,36 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
                 Rt[(size_t)row * CW + th * DS + col] = 0.f;
             }
         }
-        // (B) alpha and beta windows of the sub-tile's symbols
+        // (B) alpha and beta windows of the sub-tile's symbols, with the exact
+        // factor that undoes the chains' tilts (k_chain):
+        //   sigma ~ alpha^_i(m') beta^_{i+1}(m) 2^{(theta'_{i+1} - theta_i)(m' - mean_i)}
+        //           2^{(theta'_{i+1} - 1) j} prior R~
+        // up to a constant per symbol.  The alpha-side factor is applied in log
+        // space and clamped, so a zero alpha never meets an overflowing factor.
         for (int idx = threadIdx.x; idx < S * P; idx += blockDim.x) {
             const int il = idx / P, pl = idx - il * P;
             const long long i = ilo + il, p = p0 + pl;
             const long long s = p - (long long)n * i + xmax;
-            Aw[idx] = (s >= 0 && s < M && p <= rho) ? f.alpha[(size_t)i * f.Mp + s] : 0.f;
+            float v = 0.f;
+            if (s >= 0 && s < M && p <= rho) {
+                const float a = f.alpha[(size_t)i * f.Mp + s];
+                if (a > 0.f) {
+                    const float e = (float)((f.thb[i + 1] - f.thf[i]) *
+                                            ((double)(s - xmax) - f.mcf[i]));
+                    v = exp2f(fminf(log2f(a) + e, 126.f));
+                }
+            }
+            Aw[idx] = v;
         }
         for (int idx = threadIdx.x; idx < S * BW; idx += blockDim.x) {
             const int il = idx / BW, k = idx - il * BW;
             const long long i = ilo + il;
             const long long s = p0 - (long long)n * i + xmax - n + k;
             Bw[idx] = (s >= 0 && s < M) ? f.beta[(size_t)(i + 1) * f.Mp + s] : 0.f;
+        }
+        for (int idx = threadIdx.x; idx < S * MN; idx += blockDim.x) {
+            const int il = idx / MN, j = idx - il * MN;
+            Vj[idx] = exp2f((float)(f.thb[ilo + il + 1] - 1.0) * (float)j);
         }
         __syncthreads();
 
@@ -277,7 +296,8 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
                     const int kk = idx / S4, il = idx - kk * S4;
                     const int c = kc0 + kk;
                     const int pl = c / MN, j = c - pl * MN;
-                    AB[idx] = (il < S) ? Aw[il * P + pl] * Bw[il * BW + pl + j] : 0.f;
+                    AB[idx] = (il < S) ? Aw[il * P + pl] * Bw[il * BW + pl + j] * Vj[il * MN + j]
+                                       : 0.f;
                 }
                 __syncthreads();
                 if (KS > 1) {

