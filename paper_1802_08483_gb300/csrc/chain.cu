@@ -431,9 +431,15 @@ size_t chain_smem_bytes(const FrameDev &f) {
 cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, size_t smem,
                          cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    // Raise the opt-in limit once to the device maximum: graphs hold chain launches
+    // of several waves with different sizes, and every one must stay valid.
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     k_chain<<<nwork, kChainThreads, smem, st>>>(frames, work);
     return cudaGetLastError();
 }
