@@ -433,13 +433,22 @@ cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, si
     if (nwork <= 0) return cudaSuccess;
     // Raise the opt-in limit once to the device maximum: graphs hold chain launches
     // of several waves with different sizes, and every one must stay valid.
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
+    static int max_dyn = -1;
+    if (max_dyn < 0) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_chain);
         if (e != cudaSuccess) return e;
-        attr = true;
+        int dev = 0, optin = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        const int lim = optin - (int)fa.sharedSizeBytes;
+        e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (e != cudaSuccess) return e;
+        max_dyn = lim;
     }
+    if ((long long)smem > max_dyn) return cudaErrorInvalidValue;
     k_chain<<<nwork, kChainThreads, smem, st>>>(frames, work);
     return cudaGetLastError();
 }

@@ -6,7 +6,7 @@
 
 namespace mdk {
 
-constexpr int kMaxDynSmem = 227 * 1024;
+constexpr int kMaxDynSmem = 227 * 1024;  // producers use no static shared memory
 
 template <int NB, int IB>
 cudaError_t launch_fwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem, cudaStream_t st) {
