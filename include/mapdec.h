@@ -246,7 +246,9 @@ int64_t mapdec_batch_last_launches(mapdec_batch_t *b);
  * Device time of each phase of the last run, summed over waves (batch created
  * with MAPDEC_BATCH_TIMING; synchronises the stream).  ms[0..4] = received-bit
  * packing, forward producers (lattice + W), forward/backward chains, backward
- * producers (lattice + APP sums), finalize.
+ * producers (lattice + APP sums), finalize.  When frames need several waves,
+ * one wave's chains run on a second stream while other waves' producers run,
+ * so the phase times overlap and their sum exceeds the run's wall time.
  */
 int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms);
 

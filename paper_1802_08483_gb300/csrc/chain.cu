@@ -39,7 +39,7 @@ __global__ void k_pack(const FrameDev *__restrict__ frames, const uint8_t *const
 }
 
 // ---------------------------------------------------------------------------
-constexpr int kChainThreads = 256;
+constexpr int kChainThreads = 128;
 constexpr int kStages = 2;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
@@ -78,6 +78,8 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
 constexpr double kTiltGainMin = 0.02;  // long-run smoothing of the entropy-rate estimate
 constexpr double kTiltStepMax = 0.02;  // largest change of the tilt between two rows
 constexpr double kTiltMin = 0.2, kTiltMax = 1.6;
+constexpr int kTiltEvery = 4;    // steps between tilt updates once settled
+constexpr int kTiltSettle = 64;  // updates every step for the first steps
 
 // Geometry of chunk k of the step that consumes W_i.
 struct ChunkGeom {
@@ -119,7 +121,9 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const FrameDev &f, int dir, int 
 //   alpha^_i(m) = alpha_i(m) 2^{theta_i L} / Z_i,   beta^_i(m) = beta_i(m) 2^{-theta'_i L} / Y_i
 // with tilts theta driven toward h by the normalisers: with a tilt theta a
 // step's normaliser is about 2^{(theta - h) n}, so theta_{i+1} = theta_i -
-// g log2(c_i) / n (g = 1/(steps+1), floored at kTiltGainMin).  The producers
+// g log2(c_i) / n (g = 1/(steps+1), floored at kTiltGainMin); after the first
+// kTiltSettle steps it is updated every kTiltEvery steps from the mean log2 c of
+// the steps since.  The producers
 // already weight every received bit by 2 (theta = 1), so a step multiplies the
 // transition sums by 2^{(theta - 1) j} (j = received length) and pre-scales
 // the source row by 2^{(theta_{i+1} - theta_i)(m - mean)}; Z_i and the tilts
@@ -194,7 +198,8 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
     double logZ = 0.0;       // thread 0: log Z_i (forward) in nats
     double theta = 1.0;      // thread 0: tilt of the current row
     double mean = (dir == 0) ? 0.0 : (double)(send - xmax);  // thread 0: mean drift of it
-    double lc_prev = 0.0;    // thread 0: log2 of the last normaliser
+    double lc_prev = 0.0;    // thread 0: sum of log2 c since the last tilt update
+    int lc_cnt = 0;          // thread 0: number of steps in lc_prev
     long long steps = 0;
     if (threadIdx.x == 0) {
         if (dir == 0) { f.thf[0] = 1.0; f.mcf[0] = 0.0; }
@@ -207,18 +212,23 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
     for (long long g = 0; g < total; ++g) {
         const int i = step_symbol(g);
         const int k = (int)(g % nck);
-        if (k == 0) {
-            // start of a step: choose the tilt of the row this step produces
+        const bool update = steps < kTiltSettle || (steps % kTiltEvery) == 0;
+        if (k == 0 && update) {
+            // start of an update step: choose the tilt of the rows from here on
             if (threadIdx.x == 0) {
                 double tn = theta;
-                if (steps > 0) {
-                    const double gain = fmax(kTiltGainMin, 1.0 / (double)(steps + 1));
-                    const double d = fmin(kTiltStepMax, fmax(-kTiltStepMax, -gain * lc_prev / n));
+                if (steps > 0 && lc_cnt > 0) {
+                    const double gain =
+                        fmin(1.0, fmax(kTiltGainMin, (double)lc_cnt / (double)(steps + 1)));
+                    const double d =
+                        fmin(kTiltStepMax, fmax(-kTiltStepMax, -gain * (lc_prev / lc_cnt) / n));
                     tn = fmin(kTiltMax, fmax(kTiltMin, theta + d));
                 }
                 s_th[0] = theta;
                 s_th[1] = tn;
                 s_th[2] = mean;
+                lc_prev = 0.0;
+                lc_cnt = 0;
             }
             __syncthreads();
             th_cur = (float)s_th[0];
@@ -234,6 +244,16 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
                         cur[s] *= exp2f(dth * ((float)(s - xmax) - mc));
             }
             __syncthreads();
+        } else if (k == 0) {
+            // no update: the row keeps its tilt (backward: the transition weight of
+            // a step uses the source row's tilt, which is now th_new)
+            if (dir == 1 && th_cur != th_new) {
+                th_cur = th_new;
+                const float phi = th_cur - 1.f;
+                for (int j = threadIdx.x; j < MN; j += blockDim.x) vfac[j] = exp2f(phi * (float)j);
+                __syncthreads();
+            }
+            th_cur = th_new;
         }
         const ChunkGeom cg = chunk_geom(f, dir, i, k);
         const float *buf = stage0 + (size_t)(g % kStages) * stageFloats + cg.shift;
@@ -298,9 +318,10 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
                 }
                 theta = (double)th_new;
                 mean = cm / c;
-                lc_prev = log2(c);
-                ++steps;
+                lc_prev += log2(c);
+                ++lc_cnt;
             }
+            ++steps;
             float *row = (dir == 0) ? f.alpha + (size_t)(i + 1) * Mp : f.beta + (size_t)i * Mp;
             for (int s = threadIdx.x; s < M; s += blockDim.x) {
                 const float v = nxt[s] * inv;

@@ -105,9 +105,10 @@ int pack_codebook(const uint8_t *cb, int q, int n, std::vector<uint32_t> &out) {
 // planning
 // ---------------------------------------------------------------------------
 constexpr int kPhases = 5;  // pack, forward producers, chains, backward producers, finalize
+constexpr int kRegions = 3; // rotating scratch regions when frames need several waves
 constexpr size_t kFwdSmemBudget = 110 * 1024;
 constexpr size_t kBwdSmemBudget = 200 * 1024;
-constexpr size_t kChainSmemBudget = 96 * 1024;
+constexpr size_t kChainSmemBudget = 48 * 1024;
 
 struct FrameHost {
     mapdec_frame_desc_t d;
@@ -255,7 +256,11 @@ struct mapdec_batch {
     uint32_t *d_rxw = nullptr;
     uint32_t *d_cw = nullptr;
     float *d_scratch = nullptr;
-    size_t scratch_floats = 0;
+    size_t scratch_floats = 0;   // largest wave's scratch
+    size_t region_floats = 0;    // stride between rotating scratch regions
+    int regions = 1;
+    cudaStream_t aux_stream = nullptr;  // chains run here, overlapping the producers
+    std::vector<cudaEvent_t> dep;       // per wave: forward done, chains done
     std::vector<Wave> waves;
     std::vector<void *> allocs;
     cudaStream_t stream = nullptr;
@@ -277,6 +282,8 @@ struct mapdec_batch {
         if (gexec) cudaGraphExecDestroy(gexec);
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (aux_stream) cudaStreamDestroy(aux_stream);
+        for (cudaEvent_t e : dep) cudaEventDestroy(e);
         for (void *p : allocs) cudaFree(p);
     }
 };
@@ -346,19 +353,24 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         for (auto &h : b->fr) std::copy(h.cw.begin(), h.cw.end(), cwall.begin() + h.cw_off);
         CK(cudaMemcpy(b->d_cw, cwall.data(), cwall.size() * 4, cudaMemcpyHostToDevice));
     }
-    // scratch budget and waves (frames kept in order; a wave is a contiguous range)
+    // Scratch budget and waves (frames kept in order; a wave is a contiguous
+    // range).  If everything fits, one wave; otherwise waves rotate over three
+    // scratch regions so that a wave's chains overlap the next wave's forward
+    // producers and the previous wave's backward producers.
     size_t freeb = 0, totb = 0;
     CK(cudaMemGetInfo(&freeb, &totb));
     size_t bud = budget > 0 ? (size_t)budget : (size_t)(0.6 * (double)freeb);
-    size_t maxf = 0;
-    for (auto &h : b->fr) maxf = std::max(maxf, h.scratch_floats);
-    if (maxf * 4 > bud) bud = maxf * 4;  // at least one frame per wave
+    size_t maxf = 0, sumf = 0;
+    for (auto &h : b->fr) { maxf = std::max(maxf, h.scratch_floats); sumf += h.scratch_floats; }
+    const bool one_wave = sumf * 4 <= bud;
+    size_t wave_bud = one_wave ? bud / 4 : bud / 4 / kRegions;  // in floats
+    if (wave_bud < maxf) wave_bud = maxf;                        // at least one frame per wave
     {
         size_t acc = 0;
         Wave w;
         w.f0 = 0;
         for (int i = 0; i < nf; ++i) {
-            if (acc + b->fr[i].scratch_floats > bud / 4 && i > w.f0) {
+            if (acc + b->fr[i].scratch_floats > wave_bud && i > w.f0) {
                 w.f1 = i;
                 b->waves.push_back(w);
                 w = Wave();
@@ -371,10 +383,13 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         w.f1 = nf;
         b->waves.push_back(w);
     }
-    b->d_scratch = (float *)b->dalloc(b->scratch_floats * 4 + 256);
+    b->regions = b->waves.size() > 1 ? kRegions : 1;
+    b->region_floats = rup(b->scratch_floats, 64);
+    b->d_scratch = (float *)b->dalloc(b->region_floats * 4 * b->regions + 256);
     // per-wave descriptors and work tables
-    for (auto &w : b->waves) {
-        size_t off = 0;
+    for (size_t wi = 0; wi < b->waves.size(); ++wi) {
+        Wave &w = b->waves[wi];
+        size_t off = (wi % b->regions) * b->region_floats;
         std::vector<FrameDev> devs;
         std::vector<const uint8_t *> rxp;
         std::vector<uint32_t *> rxwp;
@@ -456,50 +471,82 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             w.cls.push_back(c);
         }
     }
+    CK(cudaStreamCreateWithFlags(&b->aux_stream, cudaStreamNonBlocking));
+    b->dep.resize(b->waves.size() * 2 + 2);
+    for (auto &e : b->dep) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (flags & MAPDEC_BATCH_TIMING) {
         b->timing = true;
-        b->events.resize(b->waves.size() * (kPhases + 1));
+        b->events.resize(b->waves.size() * kPhases * 2);
         for (auto &e : b->events) CK(cudaEventCreate(&e));
     }
     return MAPDEC_OK;
 }
 
-// Enqueue one full run on stream st.  With timing enabled an event is recorded
-// at every phase boundary (inside a captured graph as external event nodes).
-// Throws CudaErr.
+// Enqueue one full run on stream st (producers) and the batch's auxiliary
+// stream (chains).  Per wave w: pack and forward producers on st; the chains
+// on the auxiliary stream after the forward producers; the backward producers
+// and finalize on st after the chains.  The forward producers of wave w+1 are
+// issued before the backward producers of wave w, so they overlap wave w's
+// chains; the three scratch regions keep overlapping waves apart.  With
+// timing enabled, events bracket every phase of every wave (inside a captured
+// graph they become external event nodes).  Throws CudaErr.
 int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
     int64_t launches = 0;
-    CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->nframes * 4, st));
-    int wi = 0;
-    auto mark = [&](int ph) {
+    const int W = (int)b->waves.size();
+    cudaStream_t cs = b->aux_stream;
+    auto mark = [&](int w, int ph, int end, cudaStream_t s) {
         if (b->timing)
-            CK(cudaEventRecordWithFlags(b->events[(size_t)wi * (kPhases + 1) + ph], st,
+            CK(cudaEventRecordWithFlags(b->events[((size_t)w * kPhases + ph) * 2 + end], s,
                                         cudaEventRecordExternal));
     };
-    for (auto &w : b->waves) {
-        const int nw = w.f1 - w.f0;
-        mark(0);
-        CK(launch_pack(w.d_frames, w.d_rxptr, w.d_rxwptr, nw, w.max_words, st));
+    cudaEvent_t fork = b->dep[2 * W], join = b->dep[2 * W + 1];
+    CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->nframes * 4, st));
+    CK(cudaEventRecord(fork, st));
+    CK(cudaStreamWaitEvent(cs, fork, 0));
+    auto forward = [&](int w) {
+        Wave &wv = b->waves[w];
+        const int nw = wv.f1 - wv.f0;
+        mark(w, 0, 0, st);
+        CK(launch_pack(wv.d_frames, wv.d_rxptr, wv.d_rxwptr, nw, wv.max_words, st));
         ++launches;
-        mark(1);
-        for (auto &c : w.cls) {
-            CK(launch_fwd(c.n, c.I, w.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
+        mark(w, 0, 1, st);
+        mark(w, 1, 0, st);
+        for (auto &c : wv.cls) {
+            CK(launch_fwd(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
             ++launches;
         }
-        mark(2);
-        CK(launch_chain(w.d_frames, w.d_chain, w.nchain, w.smem_chain, st));
+        mark(w, 1, 1, st);
+        CK(cudaEventRecord(b->dep[2 * w], st));
+        // chains of wave w on the auxiliary stream
+        CK(cudaStreamWaitEvent(cs, b->dep[2 * w], 0));
+        mark(w, 2, 0, cs);
+        CK(launch_chain(wv.d_frames, wv.d_chain, wv.nchain, wv.smem_chain, cs));
         ++launches;
-        mark(3);
-        for (auto &c : w.cls) {
-            CK(launch_bwd(c.n, c.I, grad, w.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
+        mark(w, 2, 1, cs);
+        CK(cudaEventRecord(b->dep[2 * w + 1], cs));
+    };
+    auto backward = [&](int w) {
+        Wave &wv = b->waves[w];
+        const int nw = wv.f1 - wv.f0;
+        CK(cudaStreamWaitEvent(st, b->dep[2 * w + 1], 0));
+        mark(w, 3, 0, st);
+        for (auto &c : wv.cls) {
+            CK(launch_bwd(c.n, c.I, grad, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
             ++launches;
         }
-        mark(4);
-        CK(launch_finalize(w.d_frames, nw, grad ? 1 : 0, st));
+        mark(w, 3, 1, st);
+        mark(w, 4, 0, st);
+        CK(launch_finalize(wv.d_frames, nw, grad ? 1 : 0, st));
         ++launches;
-        mark(5);
-        ++wi;
+        mark(w, 4, 1, st);
+    };
+    forward(0);
+    for (int w = 0; w < W; ++w) {
+        if (w + 1 < W) forward(w + 1);
+        backward(w);
     }
+    CK(cudaEventRecord(join, cs));
+    CK(cudaStreamWaitEvent(st, join, 0));
     return launches;
 }
 
@@ -820,8 +867,8 @@ int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms) {
     for (size_t w = 0; w < b->waves.size(); ++w)
         for (int k = 0; k < kPhases; ++k) {
             float t = 0.f;
-            if (cudaEventElapsedTime(&t, b->events[w * (kPhases + 1) + k],
-                                     b->events[w * (kPhases + 1) + k + 1]) != cudaSuccess) {
+            if (cudaEventElapsedTime(&t, b->events[(w * kPhases + k) * 2],
+                                     b->events[(w * kPhases + k) * 2 + 1]) != cudaSuccess) {
                 cudaGetLastError();
                 return MAPDEC_ERR_CUDA;
             }
