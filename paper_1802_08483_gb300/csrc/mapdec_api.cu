@@ -107,7 +107,7 @@ int pack_codebook(const uint8_t *cb, int q, int n, std::vector<uint32_t> &out) {
 constexpr int kPhases = 5;  // pack, forward producers, chains, backward producers, finalize
 constexpr int kRegions = 3; // rotating scratch regions when frames need several waves
 constexpr size_t kFwdSmemBudget = 110 * 1024;
-constexpr size_t kBwdSmemBudget = 200 * 1024;
+constexpr size_t kBwdSmemBudget = 110 * 1024;  // two CTAs per SM
 constexpr size_t kChainSmemBudget = 48 * 1024;
 
 struct FrameHost {

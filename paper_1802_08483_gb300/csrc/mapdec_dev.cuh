@@ -139,6 +139,13 @@ __device__ __forceinline__ void lattice_unrolled(uint32_t x, uint64_t y, const f
     float wp[IB + 1], wd[IB + 1];
 #pragma unroll
     for (int a = 0; a <= IB; ++a) { wp[a] = wpow[a]; wd[a] = wder[a]; }
+    // Received bits as all-ones / all-zeros masks.  Per row the pair (A, B) =
+    // (Qdot for y = 0, Qdot for y = 1) is swapped by x_{r+1}; per node the
+    // weight is picked exactly with one bitwise select, (A & ~m_j) | (B & m_j).
+    uint32_t ym[WW];
+#pragma unroll
+    for (int j = 0; j < WW; ++j) ym[j] = 0u - (uint32_t)((y >> j) & 1u);
+    const uint32_t qs_bits = __float_as_uint(qsame), qd_bits = __float_as_uint(qdiff);
 #pragma unroll
     for (int j = 0; j <= WW; ++j) { F[j] = 0.f; if (MODE) T[j] = 0.f; }
     F[0] = 1.f;
@@ -146,7 +153,9 @@ __device__ __forceinline__ void lattice_unrolled(uint32_t x, uint64_t y, const f
     for (int r = 0; r < NB; ++r) {
         const int hiF = r * (IB + 1);        // last non-zero column of row r
         const int hiN = (r + 1) * (IB + 1);  // last non-zero column of row r+1
-        const uint64_t mm = y ^ (((x >> r) & 1u) ? ~0ull : 0ull);  // bit j-1: y_j != x_{r+1}
+        const uint32_t xm = 0u - ((x >> r) & 1u);            // x_{r+1} as a mask
+        const uint32_t qa = (qs_bits & ~xm) | (qd_bits & xm);  // Qdot(0 | x)
+        const uint32_t qb = (qd_bits & ~xm) | (qs_bits & xm);  // Qdot(1 | x)
         float gcar = 0.f, tcar = 0.f;        // G_{r,j}, TG_{r,j} at the current column
 #pragma unroll
         for (int j = WW; j >= 0; --j) {
@@ -165,15 +174,19 @@ __device__ __forceinline__ void lattice_unrolled(uint32_t x, uint64_t y, const f
                         }
                     }
                 }
-                const bool mis = (j >= 1) && ((mm >> (j >= 1 ? j - 1 : 0)) & 1ull);
-                const float Q = mis ? qdiff : qsame;
                 float f = Pd * gcar;
-                if (j >= 1) f = fmaf(Q, gprev, f);
+                float Q = 0.f;
+                const uint32_t m = (j >= 1) ? ym[j >= 1 ? j - 1 : 0] : 0u;
+                if (j >= 1) {
+                    Q = __uint_as_float((qa & ~m) | (qb & m));
+                    f = fmaf(Q, gprev, f);
+                }
                 if (MODE) {
                     float t = Pd * tcar;
                     if (j >= 1) t = fmaf(Q, tprev, t);
                     if (MODE == 2) t += gcar;
-                    if (MODE == 3 && j >= 1) t += mis ? gprev : 0.f;
+                    // substitution tangent: + G_{r,j-1} where y_j != x_{r+1}
+                    if (MODE == 3 && j >= 1) t += __uint_as_float(__float_as_uint(gprev) & (m ^ xm));
                     T[j] = t;
                     tcar = tprev;
                 }

@@ -134,12 +134,23 @@ __global__ void __launch_bounds__(kThreads) k_fwd(const FrameDev *__restrict__ f
 #pragma unroll
                 for (int t = 0; t < 4; ++t) acc[r][t] = fmaf(av[r], bv[t], acc[r][t]);
         }
+        // rows of W are contiguous in (s', j) when MNS == MN: the 4 columns of a
+        // micro-tile land on consecutive floats unless the band clips them
+        const long long pBlast = p0 + (c0 + 3 < NC ? c0 + 3 : NC - 1) / MN;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int il = il0 + r;
             if (il >= S) break;
             const long long i = ilo + il;
             float *Wi = f.W + (size_t)i * f.wblk;
+            const long long sA = pA - (long long)n * i + xmax;
+            const long long sB = pBlast - (long long)n * i + xmax;
+            if (f.MNS == MN && c0 + 3 < NC && sA >= 0 && sB < M && pBlast <= rho) {
+                float *dst = Wi + (p0 - (long long)n * i + xmax) * MN + c0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) dst[t] = acc[r][t];
+                continue;
+            }
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int c = c0 + t;
@@ -162,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd(const FrameDev *__restrict__ f
 // Per sub-tile this is a GEMM  C (S x NR*DS) = AB (S x K) * Rt (K x NR*DS),
 // K = P*MN, whose A operand AB[c][il] = alpha*beta is built in chunks.
 // smem: Rt[K][CW]  (CW = NR*DS, DS = roundup4(q); column t*DS + D)
-//       Aw[S][P], Bw[S][BW] (BW = P + MN - 1), Vj[S][MN] (tilt factor per j)
+//       Aw[S][P], Bw[S][BW] (BW = P + MN - 1), both carrying the tilt factors
 //       AB[kKC][S4] / reduction scratch
 //       Lacc[S2][q], Gacc[S2][3], Ct[3][S4][DS] (gradient mode)
 // ---------------------------------------------------------------------------
@@ -193,8 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
     float *Rt = reinterpret_cast<float *>(smem4);
     float *Aw = Rt + (size_t)K * CW;
     float *Bw = Aw + (((size_t)f.S * P + 3) & ~(size_t)3);
-    float *Vj = Bw + (((size_t)f.S * BW + 3) & ~(size_t)3);
-    float *AB = Vj + (((size_t)f.S * MN + 3) & ~(size_t)3);
+    float *AB = Bw + (((size_t)f.S * BW + 3) & ~(size_t)3);
     size_t abn = (size_t)kKC * Smax4;
     if (abn < (size_t)kThreads * 16) abn = (size_t)kThreads * 16;
     float *Lacc = AB + abn;
@@ -247,6 +257,9 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
         //           2^{(theta'_{i+1} - 1) j} prior R~
         // up to a constant per symbol.  The alpha-side factor is applied in log
         // space and clamped, so a zero alpha never meets an overflowing factor.
+        // The per-j factor 2^{phi j}, phi = theta'_{i+1} - 1, splits exactly as
+        // 2^{phi (pl + j)} 2^{-phi pl}: folded into the beta window (index pl + j)
+        // and the alpha window (index pl).
         for (int idx = threadIdx.x; idx < S * P; idx += blockDim.x) {
             const int il = idx / P, pl = idx - il * P;
             const long long i = ilo + il, p = p0 + pl;
@@ -255,8 +268,10 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
             if (s >= 0 && s < M && p <= rho) {
                 const float a = f.alpha[(size_t)i * f.Mp + s];
                 if (a > 0.f) {
+                    const double phi = f.thb[i + 1] - 1.0;
                     const float e = (float)((f.thb[i + 1] - f.thf[i]) *
-                                            ((double)(s - xmax) - f.mcf[i]));
+                                                ((double)(s - xmax) - f.mcf[i]) -
+                                            phi * (double)pl);
                     v = exp2f(fminf(log2f(a) + e, 126.f));
                 }
             }
@@ -266,11 +281,12 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
             const int il = idx / BW, k = idx - il * BW;
             const long long i = ilo + il;
             const long long s = p0 - (long long)n * i + xmax - n + k;
-            Bw[idx] = (s >= 0 && s < M) ? f.beta[(size_t)(i + 1) * f.Mp + s] : 0.f;
-        }
-        for (int idx = threadIdx.x; idx < S * MN; idx += blockDim.x) {
-            const int il = idx / MN, j = idx - il * MN;
-            Vj[idx] = exp2f((float)(f.thb[ilo + il + 1] - 1.0) * (float)j);
+            float v = 0.f;
+            if (s >= 0 && s < M) {
+                const float b = f.beta[(size_t)(i + 1) * f.Mp + s];
+                v = b * exp2f((float)(f.thb[i + 1] - 1.0) * (float)k);
+            }
+            Bw[idx] = v;
         }
         __syncthreads();
 
@@ -296,8 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
                     const int kk = idx / S4, il = idx - kk * S4;
                     const int c = kc0 + kk;
                     const int pl = c / MN, j = c - pl * MN;
-                    AB[idx] = (il < S) ? Aw[il * P + pl] * Bw[il * BW + pl + j] * Vj[il * MN + j]
-                                       : 0.f;
+                    AB[idx] = (il < S) ? Aw[il * P + pl] * Bw[il * BW + pl + j] : 0.f;
                 }
                 __syncthreads();
                 if (KS > 1) {

@@ -31,7 +31,7 @@ size_t bwd_smem_bytes(const FrameDev &f, bool grad) {
     size_t ab = (size_t)kKC * Smax4;
     if (ab < (size_t)kThreads * 16) ab = (size_t)kThreads * 16;
     size_t fl = K * NR * DS + ((f.S * (size_t)f.P + 3) & ~(size_t)3) +
-                ((f.S * BW + 3) & ~(size_t)3) + ((f.S * (size_t)f.MN + 3) & ~(size_t)3) + ab +
+                ((f.S * BW + 3) & ~(size_t)3) + ab +
                 (((size_t)f.S2 * f.q + 3) & ~(size_t)3) +
                 (((size_t)f.S2 * 3 + 3) & ~(size_t)3);
     if (grad) fl += 3 * Smax4 * DS;
