@@ -11,7 +11,8 @@
 //                holds them; the forward chain keeps the exact FP64 record of
 //                every normaliser and tilt and writes log P(Y).
 //   k_finalize : APPs (eq. L, normalised over D), d logP / d prior and the
-//                FP64 reduction of the channel-parameter gradient.
+//                FP64 reduction of the channel-parameter gradient
+//                (k_grad_reduce adds the chunks of a frame in order).
 #include "mapdec_dev.cuh"
 #include "mapdec_kernels.h"
 
@@ -353,12 +354,28 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
 }
 
 // ---------------------------------------------------------------------------
-// One CTA per frame; one warp per symbol at a time, lanes over D.
+// Finalize: one CTA per (frame, chunk of kFinChunk symbols), one warp per
+// symbol, lanes over D.  Gradient sums of a chunk go to Gc[chunk]; a second
+// kernel adds the chunks of a frame in order (deterministic).
 constexpr int kFinThreads = 256;
+constexpr int kFinChunk = 64;
+
+// Row of the APP partials of symbol i in super-tile tlo + t; the first 32 are
+// cached one per lane (warp-uniform t), further ones are computed directly.
+__device__ __forceinline__ long long lp_row(const FrameDev &f, long long myrow, int t, int tlo,
+                                            int i) {
+    const long long cached = __shfl_sync(0xffffffffu, myrow, t & 31);
+    if (t < 32) return cached;
+    int ilo, ihi;
+    super_symbols(f, tlo + t, ilo, ihi);
+    return (long long)(tlo + t) * f.S2 + (i - ilo);
+}
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__restrict__ frames,
+                                                          const Work *__restrict__ work,
                                                           int grad) {
-    const FrameDev &f = frames[blockIdx.x];
+    const Work wk = work[blockIdx.x];
+    const FrameDev &f = frames[wk.frame];
     __shared__ double red[3][32];
     if (*f.status != ST_OK) return;
     const int q = f.q, n = f.n, N = f.N, xmax = f.xmax;
@@ -370,22 +387,32 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
     const double Qm = k * Pt * (1.0 - Ps), Qs = k * Pt * Ps;
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     bool bad = false;
-    for (int i = warp; i < N; i += nw) {
+    const int i0 = wk.tile * kFinChunk, i1 = min(N, i0 + kFinChunk);
+    for (int i = i0 + warp; i < i1; i += nw) {
         long long plo = (long long)n * i - xmax, phi = (long long)n * i + xmax;
         if (plo < 0) plo = 0;
         if (phi > f.rho) phi = f.rho;
         const int tlo = (int)(plo / P2), thi = (int)(phi / P2);
+        // lane l holds the Lp row offset of super-tile tlo + l for this symbol
+        long long myrow = 0;
+        if (tlo + lane <= thi) {
+            int ilo, ihi;
+            super_symbols(f, tlo + lane, ilo, ihi);
+            myrow = (long long)(tlo + lane) * f.S2 + (i - ilo);
+        }
         double z = 0.0;
         // pass 1: unnormalised sums into app, and z = sum_D prior(D) L^u(D)
-        for (int D = lane; D < q; D += 32) {
+        for (int D0 = 0; D0 < q; D0 += 32) {
+            const int D = D0 + lane;
             float s = 0.f;
-            for (int t = tlo; t <= thi; ++t) {
-                int ilo, ihi;
-                super_symbols(f, t, ilo, ihi);
-                s += f.Lp[((size_t)t * f.S2 + (i - ilo)) * q + D];
+            for (int t = 0; t <= thi - tlo; ++t) {
+                const long long row = lp_row(f, myrow, t, tlo, i);
+                if (D < q) s += f.Lp[row * q + D];
             }
-            f.app[(size_t)i * q + D] = s;
-            z += (double)f.priors[(size_t)i * q + D] * (double)s;
+            if (D < q) {
+                f.app[(size_t)i * q + D] = s;
+                z += (double)f.priors[(size_t)i * q + D] * (double)s;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
@@ -398,36 +425,55 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
             f.app[e] = (float)((double)f.priors[e] * lu * iz);
             if (f.dpriors) f.dpriors[e] = (float)(lu * iz);
         }
-        if (grad && lane == 0) {
+        if (grad) {
             double Sw = 0.0, Sd = 0.0, Ss = 0.0;
-            for (int t = tlo; t <= thi; ++t) {
-                int ilo, ihi;
-                super_symbols(f, t, ilo, ihi);
-                const float *gp = f.Gp + ((size_t)t * f.S2 + (i - ilo)) * 3;
+            for (int t = 0; t <= thi - tlo; ++t) {
+                const long long row = lp_row(f, myrow, t, tlo, i);
+                const float *gp = f.Gp + row * 3;
                 Sw += gp[0];
                 Sd += gp[1];
                 Ss += gp[2];
             }
-            // Sw, Sd, Ss: sums with dR~/dw', dR~/dPd, dR~/dQ's.  R~ is homogeneous of
-            // degree n in (Pd, Q'm, Q's) (every bit is deleted or transmitted), so
-            // Pd dR~/dPd + Q'm dR~/dQ'm + Q's dR~/dQ's = n R~ gives the Q'm sum.
-            // Chain rule with w' = k Pi/2, Q'm = k Pt (1-Ps), Q's = k Pt Ps, Pt = 1-Pi-Pd.
-            const double Sm = ((double)n * z - Pd * Sd - Qs * Ss) / Qm;
-            g0 += (0.5 * k * Sw - k * (1.0 - Ps) * Sm - k * Ps * Ss) * iz;
-            g1 += (Sd - k * (1.0 - Ps) * Sm - k * Ps * Ss) * iz;
-            g2 += (-k * Pt * Sm + k * Pt * Ss) * iz;
+            if (lane == 0) {
+                // Sw, Sd, Ss: sums with dR~/dw', dR~/dPd, dR~/dQ's.  R~ is homogeneous
+                // of degree n in (Pd, Q'm, Q's) (every bit is deleted or transmitted),
+                // so Pd dR~/dPd + Q'm dR~/dQ'm + Q's dR~/dQ's = n R~ gives the Q'm sum.
+                // Chain rule with w' = k Pi/2, Q'm = k Pt (1-Ps), Q's = k Pt Ps, Pt = 1-Pi-Pd.
+                const double Sm = ((double)n * z - Pd * Sd - Qs * Ss) / Qm;
+                g0 += (0.5 * k * Sw - k * (1.0 - Ps) * Sm - k * Ps * Ss) * iz;
+                g1 += (Sd - k * (1.0 - Ps) * Sm - k * Ps * Ss) * iz;
+                g2 += (-k * Pt * Sm + k * Pt * Ss) * iz;
+            }
         }
     }
     if (bad && lane == 0) atomicMax(f.status, ST_ZERO);
-    if (grad && f.dchan) {
+    if (grad && f.Gc) {
         if (lane == 0) { red[0][warp] = g0; red[1][warp] = g1; red[2][warp] = g2; }
         __syncthreads();
         if (threadIdx.x < 3) {
             double s = 0.0;
             for (int w = 0; w < nw; ++w) s += red[threadIdx.x][w];
-            f.dchan[threadIdx.x] = s;
+            f.Gc[(size_t)wk.tile * 3 + threadIdx.x] = s;
         }
     }
+}
+
+// Sums the chunk gradients of every frame in chunk order.
+__global__ void k_grad_reduce(const FrameDev *__restrict__ frames, int nframes) {
+    const int fi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fi >= nframes) return;
+    const FrameDev &f = frames[fi];
+    if (!f.dchan || !f.Gc || *f.status != ST_OK) return;
+    const int nch = (f.N + kFinChunk - 1) / kFinChunk;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int c = 0; c < nch; ++c) {
+        s0 += f.Gc[3 * c];
+        s1 += f.Gc[3 * c + 1];
+        s2 += f.Gc[3 * c + 2];
+    }
+    f.dchan[0] = s0;
+    f.dchan[1] = s1;
+    f.dchan[2] = s2;
 }
 
 // ---------------------------------------------------------------------------
@@ -474,9 +520,15 @@ cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, si
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const FrameDev *frames, int nframes, int grad, cudaStream_t st) {
-    if (nframes <= 0) return cudaSuccess;
-    k_finalize<<<nframes, kFinThreads, 0, st>>>(frames, grad);
+int finalize_chunks(int N) { return (N + kFinChunk - 1) / kFinChunk; }
+
+cudaError_t launch_finalize(const FrameDev *frames, const Work *work, int nwork, int nframes,
+                            int grad, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    k_finalize<<<nwork, kFinThreads, 0, st>>>(frames, work, grad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !grad) return e;
+    k_grad_reduce<<<(nframes + 127) / 128, 128, 0, st>>>(frames, nframes);
     return cudaGetLastError();
 }
 

@@ -177,6 +177,13 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
         f.nsub /= 2;
         f.S2 = symbols_span((long long)P * f.nsub);
     }
+    if (const char *e = std::getenv("MAPDEC_FORCE_NSUB")) {  // testing override
+        const int ns = std::atoi(e);
+        if (ns >= 1 && ns <= f.nsub) {
+            f.nsub = ns;
+            f.S2 = symbols_span((long long)P * f.nsub);
+        }
+    }
     f.T = (int)((f.rho + 1 + P - 1) / P);
     f.T2 = (f.T + f.nsub - 1) / f.nsub;
     // chain chunk: all states at once if it fits, else the largest power of two
@@ -208,6 +215,7 @@ size_t frame_scratch_floats(const FrameDev &f, bool grad) {
     s += rup((size_t)f.T2 * f.S2 * f.q, 64);             // Lp
     if (grad) s += rup((size_t)f.T2 * f.S2 * 3, 64);     // Gp
     s += 3 * rup((size_t)(f.N + 1) * 2, 64);             // thf, mcf, thb (doubles)
+    if (grad) s += rup((size_t)finalize_chunks(f.N) * 3 * 2, 64);  // Gc (doubles)
     return s;
 }
 
@@ -230,6 +238,7 @@ struct Wave {
     FrameDev *d_frames = nullptr;
     std::vector<ClassLaunch> cls;
     Work *d_chain = nullptr; int nchain = 0; size_t smem_chain = 0;
+    Work *d_fin = nullptr; int nfin = 0;
     const uint8_t **d_rxptr = nullptr;
     uint32_t **d_rxwptr = nullptr;
     long long max_words = 0;
@@ -411,6 +420,8 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             f.thf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
             f.mcf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
             f.thb = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+            f.Gc = nullptr;
+            if (b->grad) { f.Gc = (double *)(base + o); o += rup((size_t)finalize_chunks(f.N) * 3 * 2, 64); }
             off += o;
             f.Rout = nullptr;
             f.app = b->d_app + h.sym_off;
@@ -445,6 +456,14 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             chain.push_back({k, 0});
             chain.push_back({k, 1});
             csm = std::max(csm, chain_smem_bytes(devs[k]));
+        }
+        {
+            std::vector<Work> fin;
+            for (int k = 0; k < nw; ++k)
+                for (int c = 0; c < finalize_chunks(devs[k].N); ++c) fin.push_back({k, c});
+            w.nfin = (int)fin.size();
+            w.d_fin = (Work *)b->dalloc(sizeof(Work) * fin.size());
+            CK(cudaMemcpy(w.d_fin, fin.data(), sizeof(Work) * fin.size(), cudaMemcpyHostToDevice));
         }
         w.nchain = (int)chain.size();
         w.smem_chain = csm;
@@ -536,7 +555,7 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         }
         mark(w, 3, 1, st);
         mark(w, 4, 0, st);
-        CK(launch_finalize(wv.d_frames, nw, grad ? 1 : 0, st));
+        CK(launch_finalize(wv.d_frames, wv.d_fin, wv.nfin, nw, grad ? 1 : 0, st));
         ++launches;
         mark(w, 4, 1, st);
     };
@@ -671,7 +690,8 @@ int static_scratch_address(void **out) {
 // uniform priors if none were given, and clears the status word (the arena
 // keeps the previous call's contents).
 __global__ void k_static_setup(FrameDev f, FrameDev *fdst, Work *fwd, int T, Work *bwd, int T2,
-                               Work *chain, const uint8_t **rxp, uint32_t **rxwp,
+                               Work *chain, Work *fin, int nfin, const uint8_t **rxp,
+                               uint32_t **rxwp,
                                const uint8_t *rx, uint32_t *rxw, uint32_t *cwdst,
                                StaticCodebook cb, int q, float *uni, long long nuni,
                                float uval, int *status) {
@@ -679,6 +699,7 @@ __global__ void k_static_setup(FrameDev f, FrameDev *fdst, Work *fwd, int T, Wor
     const long long nth = (long long)gridDim.x * blockDim.x;
     for (long long t = tid; t < T; t += nth) fwd[t] = Work{0, (int)t};
     for (long long t = tid; t < T2; t += nth) bwd[t] = Work{0, (int)t};
+    for (long long c = tid; c < nfin; c += nth) fin[c] = Work{0, (int)c};
     for (long long k = tid; k < nuni; k += nth) uni[k] = uval;
     for (long long d = tid; d < q; d += nth) cwdst[d] = cb.w[d];
     if (tid == 0) {
@@ -1043,6 +1064,8 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     const size_t o_fwd = take(sizeof(Work) * (size_t)f.T);
     const size_t o_bwd = take(sizeof(Work) * (size_t)f.T2);
     const size_t o_chain = take(sizeof(Work) * 2);
+    const int nfin = finalize_chunks(d.N);
+    const size_t o_fin = take(sizeof(Work) * (size_t)nfin);
     const size_t o_rxp = take(sizeof(void *));
     const size_t o_rxwp = take(sizeof(void *));
     const long long nwords = (d.rx_len + 31) / 32 + 4;
@@ -1071,6 +1094,7 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     f.mcf = (double *)(A + o_mcf);
     f.thb = (double *)(A + o_thb);
     f.Gp = nullptr;
+    f.Gc = nullptr;
     f.Rout = nullptr;
     f.app = app_dev;
     f.dpriors = nullptr;
@@ -1081,8 +1105,9 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     cudaStream_t s = (cudaStream_t)cuda_stream;
     FrameDev *fdev = (FrameDev *)(A + o_frame);
     Work *wf = (Work *)(A + o_fwd), *wb = (Work *)(A + o_bwd), *wc = (Work *)(A + o_chain);
+    Work *wfin = (Work *)(A + o_fin);
     const long long nuni = priors_dev ? 0 : (long long)d.N * d.q;
-    k_static_setup<<<64, 256, 0, s>>>(f, fdev, wf, f.T, wb, f.T2, wc,
+    k_static_setup<<<64, 256, 0, s>>>(f, fdev, wf, f.T, wb, f.T2, wc, wfin, nfin,
                                       (const uint8_t **)(A + o_rxp), (uint32_t **)(A + o_rxwp),
                                       rx_dev, (uint32_t *)(A + o_rxw), (uint32_t *)(A + o_cw), cb,
                                       d.q, (float *)(A + o_pri), nuni, 1.0f / (float)d.q,
@@ -1094,7 +1119,7 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     if (e == cudaSuccess) e = launch_fwd(d.n, d.I, fdev, wf, f.T, fwd_smem_bytes(f), s);
     if (e == cudaSuccess) e = launch_chain(fdev, wc, 2, chain_smem_bytes(f), s);
     if (e == cudaSuccess) e = launch_bwd(d.n, d.I, false, fdev, wb, f.T2, bwd_smem_bytes(f, false), s);
-    if (e == cudaSuccess) e = launch_finalize(fdev, 1, 0, s);
+    if (e == cudaSuccess) e = launch_finalize(fdev, wfin, nfin, 1, 0, s);
     int status = MAPDEC_OK;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, f.status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -66,6 +66,7 @@ struct FrameDev {
     // thf[i], mcf[i]: tilt and mean drift of forward row i; thb[i]: tilt of
     // backward row i.  N+1 doubles each.
     double *thf, *mcf, *thb;
+    double *Gc;      // per finalize chunk: 3 gradient partial sums (gradient mode)
     // outputs
     float *app;      // N*q
     float *dpriors;  // N*q or null

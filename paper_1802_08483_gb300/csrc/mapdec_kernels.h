@@ -27,7 +27,9 @@ cudaError_t launch_pack(const FrameDev *frames, const uint8_t *const *rx_bytes,
 size_t chain_smem_bytes(const FrameDev &f);
 cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, size_t smem,
                          cudaStream_t st);
-cudaError_t launch_finalize(const FrameDev *frames, int nframes, int grad, cudaStream_t st);
+cudaError_t launch_finalize(const FrameDev *frames, const Work *work, int nwork, int nframes,
+                            int grad, cudaStream_t st);
+int finalize_chunks(int N);  // work items (frame, chunk) per frame
 
 // per-I launchers defined in producers_i<I>.cu
 #define MAPDEC_DECLARE_I(IB)                                                                 \

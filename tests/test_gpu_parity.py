@@ -166,6 +166,31 @@ def test_batch_heterogeneous_parity(forceP, monkeypatch):
     b.close()
 
 
+def test_batch_many_supertiles_per_symbol(monkeypatch):
+    """Tiny tiles (P = 1, one sub-tile per super-tile): every symbol's APP sums
+    come from more than 32 partial rows."""
+    monkeypatch.setenv("MAPDEC_FORCE_P", "1")
+    monkeypatch.setenv("MAPDEC_FORCE_NSUB", "1")
+    rng = np.random.default_rng(91)
+    frames = [synth.make_frame(rng, 8, 6, 60, 2, 40, 0.05, 0.05, 0.01, dirichlet=True),
+              synth.make_frame(rng, 4, 4, 90, 2, 36, 0.08, 0.06, 0.01, dirichlet=True)]
+    b = mapdec.Batch(frames, flags=mapdec.MAPDEC_BATCH_GRAD)
+    rx, pr = b.concat_inputs()
+    st, app, ll = b.decode(rx, pr)
+    assert st == 0, mapdec.mapdec_strerror(st)
+    st, dchan, dpri, ll2 = b.loglik_grad(rx, pr)
+    assert st == 0
+    for k, (fr, a) in enumerate(zip(frames, b.split(app))):
+        app_ref, ll_ref = _oracle(fr)
+        check_app(a, app_ref, what=f"frame {k}")
+        check_ll(ll[k], ll_ref)
+        _, g_ref, _ = oracle.loglik_grad(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax,
+                                         fr.rx, priors=fr.priors, want_priors=False)
+        for c in range(3):
+            assert abs(dchan[k, c] - g_ref[c]) <= 1e-4 * max(1.0, abs(g_ref[c]))
+    b.close()
+
+
 def test_batch_waves_match_single_wave():
     frames = _mixed_frames(8, seed=78)
     b1 = mapdec.Batch(frames, flags=0)
