@@ -163,7 +163,21 @@ enum {
     MAPDEC_BATCH_GRAPH = 1,  /* capture the launch sequence in a CUDA graph */
     MAPDEC_BATCH_PLAIN = 2,  /* one frame per launch, default tile sizes, no graph */
     MAPDEC_BATCH_GRAD = 4,   /* allocate for mapdec_batch_loglik_grad */
-    MAPDEC_BATCH_TIMING = 8  /* record CUDA events at phase boundaries of every run */
+    MAPDEC_BATCH_TIMING = 8, /* record CUDA events at phase boundaries of every run */
+    /*
+     * Checkpoint and recompute (not in the paper, which keeps every forward
+     * and backward row of Sec. II-C in memory): each frame is cut into
+     * segments of K = ceil(sqrt(N)) symbols (environment MAPDEC_SEG_K
+     * overrides K).  A first sweep runs the forward recursion segment by
+     * segment, keeping only the row at every segment boundary and the tilt
+     * record; a second sweep, last segment first, recomputes the segment's
+     * transition weights and forward rows from its checkpoint (the same rows,
+     * bit for bit) beside the backward recursion, then the APPs of that
+     * segment.  Scratch per frame falls from O(N) rows to O(K + N/K) rows at
+     * the price of computing the transition weights twice.  Results equal
+     * the unsegmented run's to rounding order of the APP partial sums.
+     */
+    MAPDEC_BATCH_SEGMENTED = 16
 };
 
 typedef struct mapdec_batch mapdec_batch_t;
@@ -248,7 +262,9 @@ int64_t mapdec_batch_last_launches(mapdec_batch_t *b);
  * packing, forward producers (lattice + W), forward/backward chains, backward
  * producers (lattice + APP sums), finalize.  When frames need several waves,
  * one wave's chains run on a second stream while other waves' producers run,
- * so the phase times overlap and their sum exceeds the run's wall time.
+ * so the phase times overlap and their sum exceeds the run's wall time.  In
+ * a MAPDEC_BATCH_SEGMENTED batch ms[1] is the whole recording sweep, ms[3]
+ * the whole recompute sweep and ms[2], ms[4] are 0.
  */
 int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms);
 

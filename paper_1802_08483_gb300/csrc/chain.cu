@@ -134,13 +134,18 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
                                                          const Work *__restrict__ work) {
     const Work wk = work[blockIdx.x];
     const FrameDev &f = frames[wk.frame];
-    const int dir = wk.tile;  // 0 = forward (alpha), 1 = backward (beta)
+    const int dir = wk.tile & 1;  // 0 = forward (alpha), 1 = backward (beta); bit 1: replay
     const int M = f.M, Mp = f.Mp, MNS = f.MNS, MN = f.MN, n = f.n, N = f.N, xmax = f.xmax;
     const long long rho = f.rho;
     const int CD = f.chainCD;
     const int nck = (M + CD - 1) / CD;
-    const long long total = (long long)N * nck;
+    const int i0 = f.seg_i0, i1 = f.seg_i1;  // symbols of this launch (segment)
+    const long long total = (long long)(i1 - i0) * nck;
     const int send = (int)(rho - (long long)n * N) + xmax;  // state of the end drift
+    const bool segm = (f.chain_flags & CH_SEGMENTED) != 0;
+    const bool replay = dir == 0 && (wk.tile & 2) != 0;
+    // first launch of this direction: the frame boundary; otherwise the row carried over
+    const bool fresh = dir == 0 ? (i0 == 0) : (i1 == N);
 
     __shared__ uint64_t bar[kStages];
     __shared__ double red[64];
@@ -152,7 +157,10 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
     const size_t stageFloats = ((size_t)(CD + MN + 1) * MNS + 8 + 3) & ~(size_t)3;
 
     for (int s = threadIdx.x; s < Mp; s += blockDim.x) {
-        cur[s] = (s == (dir == 0 ? xmax : send)) ? 1.f : 0.f;
+        float v;
+        if (fresh) v = (s == (dir == 0 ? xmax : send)) ? 1.f : 0.f;
+        else v = (dir == 0) ? f.ckpt[s] : f.bedge[s];
+        cur[s] = v;
         nxt[s] = 0.f;
     }
     if (threadIdx.x == 0) {
@@ -162,18 +170,18 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
     }
     __syncthreads();
     {
-        float *row0 = (dir == 0) ? f.alpha : f.beta + (size_t)N * Mp;
+        float *row0 = (dir == 0) ? f.alpha + (size_t)i0 * Mp : f.beta + (size_t)i1 * Mp;
         for (int s = threadIdx.x; s < Mp; s += blockDim.x) row0[s] = cur[s];
     }
     auto step_symbol = [&](long long g) -> int {
         const int st = (int)(g / nck);
-        return dir == 0 ? st : N - 1 - st;
+        return dir == 0 ? i0 + st : i1 - 1 - st;
     };
     // Self-check of every copy: source inside this frame's W, destination inside
     // its stage, 16-byte alignment and size.  A violation records ST_ARG in the
     // frame status and completes the stage's phase with a plain arrive instead.
-    const float *wlo = f.W;
-    const float *whi = f.W + (size_t)N * f.wblk + 16;
+    const float *wlo = f.W + (size_t)i0 * f.wblk;
+    const float *whi = f.W + (size_t)i1 * f.wblk + 16;
     auto issue = [&](long long g) {
         const int i = step_symbol(g);
         const int k = (int)(g % nck);
@@ -201,22 +209,53 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
     double mean = (dir == 0) ? 0.0 : (double)(send - xmax);  // thread 0: mean drift of it
     double lc_prev = 0.0;    // thread 0: sum of log2 c since the last tilt update
     int lc_cnt = 0;          // thread 0: number of steps in lc_prev
-    long long steps = 0;
-    if (threadIdx.x == 0) {
+    long long steps = 0;     // every thread: steps taken in this direction so far
+    if (!fresh && segm) {
+        const ChainState &cs = f.cst[dir];
+        steps = cs.steps;
+        if (threadIdx.x == 0) {
+            theta = cs.theta;
+            mean = cs.mean;
+            logZ = cs.logZ;
+            lc_prev = cs.lc_sum;
+            lc_cnt = cs.lc_cnt;
+        }
+    }
+    if (replay) steps = i0;
+    if (threadIdx.x == 0 && fresh && !replay) {
         if (dir == 0) { f.thf[0] = 1.0; f.mcf[0] = 0.0; }
         else f.thb[N] = 1.0;
     }
     double part = 0.0, partm = 0.0;  // this thread's share of the normaliser and first moment
     float th_cur = 1.f, th_new = 1.f, mc = 0.f;
+    if (!fresh && segm && !replay) {
+        // continuing a recursion: the first step here need not be an update
+        // step, so restore the row's tilt and its transition weights as the
+        // previous launch left them
+        if (threadIdx.x == 0) {
+            s_th[0] = theta;
+            s_th[2] = mean;
+        }
+        __syncthreads();
+        th_cur = th_new = (float)s_th[0];
+        mc = (float)s_th[2];
+        for (int j = threadIdx.x; j < MN; j += blockDim.x) vfac[j] = exp2f((th_cur - 1.f) * (float)j);
+        __syncthreads();
+    }
     bool failed = false;
     long long gfail = 0;
     for (long long g = 0; g < total; ++g) {
         const int i = step_symbol(g);
         const int k = (int)(g % nck);
-        const bool update = steps < kTiltSettle || (steps % kTiltEvery) == 0;
+        const bool update = replay || steps < kTiltSettle || (steps % kTiltEvery) == 0;
         if (k == 0 && update) {
             // start of an update step: choose the tilt of the rows from here on
-            if (threadIdx.x == 0) {
+            // (the recompute sweep replays the tilts recorded by the first sweep)
+            if (threadIdx.x == 0 && replay) {
+                s_th[0] = f.thf[i];
+                s_th[1] = f.thf[i + 1];
+                s_th[2] = f.mcf[i];
+            } else if (threadIdx.x == 0) {
                 double tn = theta;
                 if (steps > 0 && lc_cnt > 0) {
                     const double gain =
@@ -310,11 +349,11 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
             const float inv = (float)(1.0 / c);
             if (threadIdx.x == 0) {
                 const double dth = (double)th_new - (double)th_cur;
-                if (dir == 0) {
+                if (dir == 0 && !replay) {
                     logZ += log(c) + dth * ((double)n * i + (double)mc) * 0.6931471805599453;
                     f.thf[i + 1] = (double)th_new;
                     f.mcf[i + 1] = cm / c;
-                } else {
+                } else if (dir == 1) {
                     f.thb[i] = (double)th_new;
                 }
                 theta = (double)th_new;
@@ -343,7 +382,21 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
         __syncthreads();
         return;
     }
-    if (dir == 0 && threadIdx.x == 0) {
+    if (segm && !replay) {
+        // carry the boundary row and the controller state to the next launch
+        float *edge = (dir == 0) ? f.ckpt + Mp : f.bedge;
+        for (int s = threadIdx.x; s < Mp; s += blockDim.x) edge[s] = cur[s];
+        if (threadIdx.x == 0) {
+            ChainState &cs = f.cst[dir];
+            cs.theta = theta;
+            cs.mean = mean;
+            cs.logZ = logZ;
+            cs.lc_sum = lc_prev;
+            cs.lc_cnt = lc_cnt;
+            cs.steps = steps;
+        }
+    }
+    if (dir == 0 && !replay && i1 == N && threadIdx.x == 0) {
         const float aN = cur[send];
         if (!(aN > 0.f)) {
             atomicMax(f.status, ST_ZERO);
@@ -387,7 +440,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
     const double Qm = k * Pt * (1.0 - Ps), Qs = k * Pt * Ps;
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     bool bad = false;
-    const int i0 = wk.tile * kFinChunk, i1 = min(N, i0 + kFinChunk);
+    const int i0 = f.seg_i0 + (wk.tile - f.fin_base) * kFinChunk;
+    const int i1 = min(f.seg_i1, i0 + kFinChunk);
     for (int i = i0 + warp; i < i1; i += nw) {
         long long plo = (long long)n * i - xmax, phi = (long long)n * i + xmax;
         if (plo < 0) plo = 0;
@@ -464,7 +518,7 @@ __global__ void k_grad_reduce(const FrameDev *__restrict__ frames, int nframes) 
     if (fi >= nframes) return;
     const FrameDev &f = frames[fi];
     if (!f.dchan || !f.Gc || *f.status != ST_OK) return;
-    const int nch = (f.N + kFinChunk - 1) / kFinChunk;
+    const int nch = f.fin_total;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int c = 0; c < nch; ++c) {
         s0 += f.Gc[3 * c];
@@ -521,13 +575,13 @@ cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, si
 }
 
 int finalize_chunks(int N) { return (N + kFinChunk - 1) / kFinChunk; }
+size_t chain_state_bytes() { return sizeof(ChainState); }
 
 cudaError_t launch_finalize(const FrameDev *frames, const Work *work, int nwork, int nframes,
-                            int grad, cudaStream_t st) {
-    if (nwork <= 0) return cudaSuccess;
-    k_finalize<<<nwork, kFinThreads, 0, st>>>(frames, work, grad);
+                            int grad, cudaStream_t st, bool reduce) {
+    if (nwork > 0) k_finalize<<<nwork, kFinThreads, 0, st>>>(frames, work, grad);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !grad) return e;
+    if (e != cudaSuccess || !grad || !reduce || nframes <= 0) return e;
     k_grad_reduce<<<(nframes + 127) / 128, 128, 0, st>>>(frames, nframes);
     return cudaGetLastError();
 }

@@ -120,6 +120,7 @@ struct FrameHost {
     FrameDev dev{};         // shape, constants; pointers filled per wave
     size_t scratch_floats = 0;
     double cost = 0.0;
+    int segK = 0, nseg = 1; // segmented mode: symbols per segment, segments
 };
 
 // Fill shape-dependent fields of dev (P, S, T, nsub, ...) for received length rho.
@@ -146,6 +147,14 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     f.dPi = d.Pi; f.dPd = d.Pd; f.dPs = d.Ps; f.dPt = Pt;
     f.kappa = kappa;
     f.logk = std::log(kappa);
+    f.seg_i0 = 0;
+    f.seg_i1 = d.N;
+    f.fin_base = 0;
+    f.fin_total = finalize_chunks(d.N);
+    f.chain_flags = 0;
+    f.ckpt = nullptr;
+    f.bedge = nullptr;
+    f.cst = nullptr;
 
     auto symbols_span = [&](long long Ppos) -> int {
         return (int)((Ppos - 1 + 2LL * d.xmax) / d.n + 2);
@@ -219,6 +228,28 @@ size_t frame_scratch_floats(const FrameDev &f, bool grad) {
     return s;
 }
 
+// Segmented mode: W, alpha, beta and the APP partials for one segment of K
+// symbols, plus forward checkpoints every K symbols.
+int seg_supertiles(const FrameDev &f, int K) {
+    const long long P2 = (long long)f.P * f.nsub;
+    return (int)(((long long)f.n * K + 2LL * f.xmax) / P2 + 3);
+}
+size_t frame_scratch_floats_seg(const FrameDev &f, int K, int S, bool grad) {
+    const int T2s = seg_supertiles(f, K);
+    const int cps = finalize_chunks(K);
+    size_t s = 0;
+    s += rup((size_t)K * f.wblk + 16, 64);               // W of one segment
+    s += rup((size_t)(K + 1) * f.Mp, 64) * 2;            // alpha, beta rows of one segment
+    s += rup((size_t)T2s * f.S2 * f.q, 64);              // Lp of one segment
+    if (grad) s += rup((size_t)T2s * f.S2 * 3, 64);      // Gp
+    s += 3 * rup((size_t)(f.N + 1) * 2, 64);             // thf, mcf, thb
+    if (grad) s += rup((size_t)S * cps * 3 * 2, 64);     // Gc
+    s += rup((size_t)(S + 1) * f.Mp, 64);                // forward checkpoints
+    s += rup((size_t)f.Mp, 64);                          // backward boundary row
+    s += rup(2 * chain_state_bytes() / 4 + 1, 64);       // chain states
+    return s;
+}
+
 double frame_cost(const FrameDev &f) {
     // algorithmic flop estimate used for load balancing and reporting
     const double cells = (f.I + 1) * f.n * (f.n + 1) / 2.0 + (f.n + 1);
@@ -233,8 +264,19 @@ struct ClassLaunch {
     Work *d_bwd = nullptr; int nbwd = 0; size_t smem_bwd = 0;
 };
 
+// One segment index of a segmented wave: descriptors and work lists.
+struct SegLaunch {
+    FrameDev *d_frames = nullptr;
+    std::vector<ClassLaunch> cls;
+    Work *d_rec = nullptr; int nrec = 0;    // forward chains (record)
+    Work *d_bw = nullptr; int nbw = 0;      // forward replay + backward chains
+    Work *d_fin = nullptr; int nfin = 0;
+    int nframes = 0;
+};
+
 struct Wave {
     int f0 = 0, f1 = 0;
+    std::vector<SegLaunch> segs;  // segmented mode
     FrameDev *d_frames = nullptr;
     std::vector<ClassLaunch> cls;
     Work *d_chain = nullptr; int nchain = 0; size_t smem_chain = 0;
@@ -279,7 +321,8 @@ struct mapdec_batch {
     int64_t last_launches = 0;
     int64_t launches_per_run[2] = {0, 0};
     bool timing = false;
-    std::vector<cudaEvent_t> events;  // per wave: kPhases + 1 boundaries
+    bool segmented = false;
+    std::vector<cudaEvent_t> events;  // per wave and phase: begin, end
 
     void *dalloc(size_t bytes) {
         void *p = nullptr;
@@ -315,6 +358,81 @@ struct mapdec {
 
 namespace {
 
+// Segmented mode: per segment index, one descriptor per frame (bounds and
+// buffer bases shifted so that absolute symbol, row and super-tile indices land
+// in the frame's one-segment buffers) and the work lists of that segment.
+void build_segments(mapdec_batch *b, Wave &w, const std::vector<FrameDev> &devs,
+                    const std::map<std::pair<int, int>, std::vector<int>> &byclass) {
+    const int nw = w.f1 - w.f0;
+    int Smax = 0;
+    for (int k = 0; k < nw; ++k) Smax = std::max(Smax, b->fr[w.f0 + k].nseg);
+    w.segs.resize(Smax);
+    for (int s = 0; s < Smax; ++s) {
+        SegLaunch &sl = w.segs[s];
+        std::vector<FrameDev> sd(devs);
+        std::vector<Work> rec, bw, fin;
+        for (int k = 0; k < nw; ++k) {
+            const FrameHost &h = b->fr[w.f0 + k];
+            if (s >= h.nseg) continue;
+            FrameDev f = devs[k];
+            const int K = h.segK, i0 = s * K, i1 = std::min(f.N, i0 + K);
+            const long long P2 = (long long)f.P * f.nsub;
+            const long long plo = std::max(0LL, (long long)f.n * i0 - f.xmax);
+            const long long t2first = plo / P2;
+            auto shift = [](void *p, long long bytes) {
+                return (void *)((char *)p - bytes);
+            };
+            f.seg_i0 = i0;
+            f.seg_i1 = i1;
+            f.W = (float *)shift(devs[k].W, (long long)i0 * f.wblk * 4);
+            f.alpha = (float *)shift(devs[k].alpha, (long long)i0 * f.Mp * 4);
+            f.beta = (float *)shift(devs[k].beta, (long long)i0 * f.Mp * 4);
+            f.Lp = (float *)shift(devs[k].Lp, t2first * f.S2 * f.q * 4);
+            if (devs[k].Gp) f.Gp = (float *)shift(devs[k].Gp, t2first * f.S2 * 3 * 4);
+            f.ckpt = devs[k].ckpt + (size_t)s * f.Mp;
+            f.fin_base = s * finalize_chunks(K);
+            sd[k] = f;
+            rec.push_back({k, 0});
+            bw.push_back({k, 2});
+            bw.push_back({k, 1});
+            for (int c = 0; c < finalize_chunks(i1 - i0); ++c) fin.push_back({k, f.fin_base + c});
+        }
+        sl.nframes = nw;
+        sl.d_frames = (FrameDev *)b->dalloc(sizeof(FrameDev) * nw);
+        CK(cudaMemcpy(sl.d_frames, sd.data(), sizeof(FrameDev) * nw, cudaMemcpyHostToDevice));
+        auto upload = [&](const std::vector<Work> &v, Work *&dst, int &cnt) {
+            cnt = (int)v.size();
+            dst = (Work *)b->dalloc(sizeof(Work) * std::max<size_t>(v.size(), 1));
+            if (!v.empty())
+                CK(cudaMemcpy(dst, v.data(), sizeof(Work) * v.size(), cudaMemcpyHostToDevice));
+        };
+        upload(rec, sl.d_rec, sl.nrec);
+        upload(bw, sl.d_bw, sl.nbw);
+        upload(fin, sl.d_fin, sl.nfin);
+        for (const auto &kv : byclass) {
+            ClassLaunch c;
+            c.n = kv.first.first;
+            c.I = kv.first.second;
+            std::vector<Work> fw, bwk;
+            for (int k : kv.second) {
+                const FrameHost &h = b->fr[w.f0 + k];
+                if (s >= h.nseg) continue;
+                const FrameDev &f = sd[k];
+                const long long P2 = (long long)f.P * f.nsub;
+                const long long plo = std::max(0LL, (long long)f.n * f.seg_i0 - f.xmax);
+                const long long phi = std::min(f.rho, (long long)f.n * (f.seg_i1 - 1) + f.xmax);
+                for (long long t = plo / f.P; t <= phi / f.P; ++t) fw.push_back({k, (int)t});
+                for (long long t = plo / P2; t <= phi / P2; ++t) bwk.push_back({k, (int)t});
+                c.smem_fwd = std::max(c.smem_fwd, fwd_smem_bytes(f));
+                c.smem_bwd = std::max(c.smem_bwd, bwd_smem_bytes(f, b->grad));
+            }
+            upload(fw, c.d_fwd, c.nfwd);
+            upload(bwk, c.d_bwd, c.nbwd);
+            sl.cls.push_back(c);
+        }
+    }
+}
+
 // Build the batch: plan, allocate, upload descriptors.  Throws CudaErr.
 int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int flags,
                 int64_t budget, int forceP) {
@@ -334,7 +452,19 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         if (st) return st;
         h.d.codebook = nullptr;
         plan_shape(h.dev, h.d, b->grad, (flags & MAPDEC_BATCH_PLAIN) ? 0 : forceP);
-        h.scratch_floats = frame_scratch_floats(h.dev, b->grad);
+        if (flags & MAPDEC_BATCH_SEGMENTED) {
+            int K = (int)std::ceil(std::sqrt((double)h.d.N));
+            if (const char *e = std::getenv("MAPDEC_SEG_K")) {  // tuning / testing override
+                const int k2 = std::atoi(e);
+                if (k2 >= 1) K = k2;
+            }
+            K = std::max(1, std::min(K, h.d.N));
+            h.segK = K;
+            h.nseg = (h.d.N + K - 1) / K;
+            h.scratch_floats = frame_scratch_floats_seg(h.dev, K, h.nseg, b->grad);
+        } else {
+            h.scratch_floats = frame_scratch_floats(h.dev, b->grad);
+        }
         h.cost = frame_cost(h.dev);
         h.rx_off = b->rx_total;
         b->rx_total += h.d.rx_len;  // dense: the caller's concatenation, one copy
@@ -396,6 +526,8 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
     b->region_floats = rup(b->scratch_floats, 64);
     b->d_scratch = (float *)b->dalloc(b->region_floats * 4 * b->regions + 256);
     // per-wave descriptors and work tables
+    const bool segmented = (flags & MAPDEC_BATCH_SEGMENTED) != 0;
+    b->segmented = segmented;
     for (size_t wi = 0; wi < b->waves.size(); ++wi) {
         Wave &w = b->waves[wi];
         size_t off = (wi % b->regions) * b->region_floats;
@@ -411,17 +543,40 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             f.priors = b->d_priors + h.sym_off;
             float *base = b->d_scratch + off;
             size_t o = 0;
-            f.W = base + o; o += rup((size_t)f.N * f.wblk + 16, 64);
-            f.alpha = base + o; o += rup((size_t)(f.N + 1) * f.Mp, 64);
-            f.beta = base + o; o += rup((size_t)(f.N + 1) * f.Mp, 64);
-            f.Lp = base + o; o += rup((size_t)f.T2 * f.S2 * f.q, 64);
-            f.Gp = nullptr;
-            if (b->grad) { f.Gp = base + o; o += rup((size_t)f.T2 * f.S2 * 3, 64); }
-            f.thf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
-            f.mcf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
-            f.thb = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
-            f.Gc = nullptr;
-            if (b->grad) { f.Gc = (double *)(base + o); o += rup((size_t)finalize_chunks(f.N) * 3 * 2, 64); }
+            if (!segmented) {
+                f.W = base + o; o += rup((size_t)f.N * f.wblk + 16, 64);
+                f.alpha = base + o; o += rup((size_t)(f.N + 1) * f.Mp, 64);
+                f.beta = base + o; o += rup((size_t)(f.N + 1) * f.Mp, 64);
+                f.Lp = base + o; o += rup((size_t)f.T2 * f.S2 * f.q, 64);
+                f.Gp = nullptr;
+                if (b->grad) { f.Gp = base + o; o += rup((size_t)f.T2 * f.S2 * 3, 64); }
+                f.thf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+                f.mcf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+                f.thb = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+                f.Gc = nullptr;
+                if (b->grad) { f.Gc = (double *)(base + o); o += rup((size_t)finalize_chunks(f.N) * 3 * 2, 64); }
+            } else {
+                // buffers of one segment; per-segment descriptors shift their bases
+                const int K = h.segK, S = h.nseg;
+                const int T2s = seg_supertiles(f, K), cps = finalize_chunks(K);
+                f.W = base + o; o += rup((size_t)K * f.wblk + 16, 64);
+                f.alpha = base + o; o += rup((size_t)(K + 1) * f.Mp, 64);
+                f.beta = base + o; o += rup((size_t)(K + 1) * f.Mp, 64);
+                f.Lp = base + o; o += rup((size_t)T2s * f.S2 * f.q, 64);
+                f.Gp = nullptr;
+                if (b->grad) { f.Gp = base + o; o += rup((size_t)T2s * f.S2 * 3, 64); }
+                f.thf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+                f.mcf = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+                f.thb = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
+                f.Gc = nullptr;
+                if (b->grad) { f.Gc = (double *)(base + o); o += rup((size_t)S * cps * 3 * 2, 64); }
+                f.ckpt = base + o; o += rup((size_t)(S + 1) * f.Mp, 64);
+                f.bedge = base + o; o += rup((size_t)f.Mp, 64);
+                f.cst = (ChainState *)(base + o); o += rup(2 * chain_state_bytes() / 4 + 1, 64);
+                f.chain_flags = CH_SEGMENTED;
+                // chunk slots s*cps + c; only the last segment can be short
+                f.fin_total = (S - 1) * cps + finalize_chunks(f.N - (S - 1) * K);
+            }
             off += o;
             f.Rout = nullptr;
             f.app = b->d_app + h.sym_off;
@@ -489,6 +644,7 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             CK(cudaMemcpy(c.d_bwd, bw.data(), sizeof(Work) * bw.size(), cudaMemcpyHostToDevice));
             w.cls.push_back(c);
         }
+        if (segmented) build_segments(b, w, devs, byclass);
     }
     CK(cudaStreamCreateWithFlags(&b->aux_stream, cudaStreamNonBlocking));
     b->dep.resize(b->waves.size() * 2 + 2);
@@ -556,7 +712,7 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         mark(w, 3, 1, st);
         mark(w, 4, 0, st);
         CK(launch_finalize(wv.d_frames, wv.d_fin, wv.nfin, nw, grad ? 1 : 0, st));
-        ++launches;
+        launches += grad ? 2 : 1;
         mark(w, 4, 1, st);
     };
     forward(0);
@@ -569,11 +725,81 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
     return launches;
 }
 
+// Segmented run (checkpoint and recompute), all on stream st.  Per wave: pack;
+// a recording sweep over the segments in order (forward producers of the
+// segment, then the forward chains, which write the tilts and a checkpoint row
+// at every segment boundary); then a sweep over the segments in reverse, each
+// recomputing its W, replaying the forward chain from its checkpoint with the
+// recorded tilts (bit-identical rows) next to the backward chain, then the APP
+// producers and finalize of the segment.  The gradient chunks are added up
+// after the last (first) segment.  Timing phases: pack, recording sweep
+// (forward), backward sweep (backward); chains and finalize read 0.
+int64_t enqueue_run_seg(mapdec_batch *b, bool grad, cudaStream_t st) {
+    int64_t launches = 0;
+    const int W = (int)b->waves.size();
+    auto mark = [&](int w, int ph, int end) {
+        if (b->timing)
+            CK(cudaEventRecordWithFlags(b->events[((size_t)w * kPhases + ph) * 2 + end], st,
+                                        cudaEventRecordExternal));
+    };
+    CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->nframes * 4, st));
+    for (int w = 0; w < W; ++w) {
+        Wave &wv = b->waves[w];
+        const int nw = wv.f1 - wv.f0;
+        const int S = (int)wv.segs.size();
+        mark(w, 0, 0);
+        CK(launch_pack(wv.d_frames, wv.d_rxptr, wv.d_rxwptr, nw, wv.max_words, st));
+        ++launches;
+        mark(w, 0, 1);
+        mark(w, 1, 0);
+        for (int s = 0; s < S; ++s) {
+            SegLaunch &sl = wv.segs[s];
+            for (auto &c : sl.cls) {
+                if (c.nfwd == 0) continue;
+                CK(launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
+                ++launches;
+            }
+            CK(launch_chain(sl.d_frames, sl.d_rec, sl.nrec, wv.smem_chain, st));
+            ++launches;
+        }
+        mark(w, 1, 1);
+        mark(w, 2, 0);
+        mark(w, 2, 1);
+        mark(w, 3, 0);
+        for (int s = S - 1; s >= 0; --s) {
+            SegLaunch &sl = wv.segs[s];
+            for (auto &c : sl.cls) {
+                if (c.nfwd == 0) continue;
+                CK(launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
+                ++launches;
+            }
+            CK(launch_chain(sl.d_frames, sl.d_bw, sl.nbw, wv.smem_chain, st));
+            ++launches;
+            for (auto &c : sl.cls) {
+                if (c.nbwd == 0) continue;
+                CK(launch_bwd(c.n, c.I, grad, sl.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
+                ++launches;
+            }
+            CK(launch_finalize(sl.d_frames, sl.d_fin, sl.nfin, nw, grad ? 1 : 0, st,
+                               grad && s == 0));
+            launches += (grad && s == 0) ? 2 : 1;
+        }
+        mark(w, 3, 1);
+        mark(w, 4, 0);
+        mark(w, 4, 1);
+    }
+    return launches;
+}
+
+int64_t enqueue_any(mapdec_batch *b, bool grad, cudaStream_t st) {
+    return b->segmented ? enqueue_run_seg(b, grad, st) : enqueue_run(b, grad, st);
+}
+
 int run_batch(mapdec_batch *b, bool grad) {
     if (grad && !b->grad) return MAPDEC_ERR_ARG;
     const bool use_graph = (b->flags & MAPDEC_BATCH_GRAPH) && !(b->flags & MAPDEC_BATCH_PLAIN);
     if (!use_graph) {
-        b->last_launches = enqueue_run(b, grad, b->stream);
+        b->last_launches = enqueue_any(b, grad, b->stream);
         return MAPDEC_OK;
     }
     if (!b->gexec || b->graph_grad != grad) {
@@ -584,7 +810,7 @@ int run_batch(mapdec_batch *b, bool grad) {
         CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
         int64_t l = 0;
         try {
-            l = enqueue_run(b, grad, b->cap_stream);
+            l = enqueue_any(b, grad, b->cap_stream);
         } catch (CudaErr &e) {
             cudaStreamEndCapture(b->cap_stream, &g);
             if (g) cudaGraphDestroy(g);

@@ -13,6 +13,10 @@
 
 namespace mdk {
 
+// chain_flags
+constexpr int CH_SEGMENTED = 1;   // start/end rows and controller state come from ckpt/bedge/cst
+constexpr int CH_REPLAY = 2;      // forward chain replays the recorded tilts (recompute sweep)
+
 constexpr int kMaxI = 7;        // insertion cap supported by the kernels
 constexpr int kMaxMN = 64;      // n(I+1) + 1 <= 64 (received window fits 64 bits)
 constexpr int kThreads = 256;   // producer block size
@@ -21,6 +25,14 @@ constexpr int kThreads = 256;   // producer block size
 enum : int {
     ST_OK = 0, ST_ARG = 1, ST_DRIFT = 2, ST_ZERO = 3, ST_NOMEM = 4, ST_CUDA = 5,
     ST_TIMEOUT = 6, ST_UNSUPPORTED = 7
+};
+
+// Chain state carried between the segment launches of a frame (segmented mode).
+struct ChainState {
+    double theta, mean, logZ, lc_sum;
+    int lc_cnt;
+    int pad;
+    long long steps;
 };
 
 // One frame as the kernels see it.  All pointers are device pointers.
@@ -67,6 +79,17 @@ struct FrameDev {
     // backward row i.  N+1 doubles each.
     double *thf, *mcf, *thb;
     double *Gc;      // per finalize chunk: 3 gradient partial sums (gradient mode)
+    // Segments.  A descriptor covers the symbols [seg_i0, seg_i1); W, alpha,
+    // beta, Lp and Gp point at buffers sized for that range, with base pointers
+    // shifted so that absolute indices land in them.  The whole frame is one
+    // segment (0, N) outside the segmented mode.
+    int seg_i0, seg_i1;
+    int fin_base;    // finalize chunk index of this segment's first chunk
+    int fin_total;   // finalize chunks of the whole frame (gradient reduction)
+    int chain_flags; // CH_* below
+    float *ckpt;     // forward checkpoint rows (segmented mode): row s at s*Mp
+    float *bedge;    // backward boundary row carried between segments (Mp floats)
+    ChainState *cst; // [0] forward, [1] backward (segmented mode)
     // outputs
     float *app;      // N*q
     float *dpriors;  // N*q or null
@@ -92,8 +115,8 @@ __host__ __device__ inline void range_symbols(const FrameDev &f, long long p0, l
     if (p1 > f.rho) p1 = f.rho;
     long long lo = ceildiv(p0 - f.xmax, f.n);
     long long hi = floordiv(p1 + f.xmax, f.n);
-    if (lo < 0) lo = 0;
-    if (hi > f.N - 1) hi = f.N - 1;
+    if (lo < f.seg_i0) lo = f.seg_i0;
+    if (hi > f.seg_i1 - 1) hi = f.seg_i1 - 1;
     ilo = (int)lo;
     ihi = (int)hi;
 }

@@ -28,7 +28,8 @@ size_t chain_smem_bytes(const FrameDev &f);
 cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_finalize(const FrameDev *frames, const Work *work, int nwork, int nframes,
-                            int grad, cudaStream_t st);
+                            int grad, cudaStream_t st, bool reduce = true);
+size_t chain_state_bytes();
 int finalize_chunks(int N);  // work items (frame, chunk) per frame
 
 // per-I launchers defined in producers_i<I>.cu

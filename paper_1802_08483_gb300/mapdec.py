@@ -33,6 +33,7 @@ MAPDEC_BATCH_GRAPH = 1
 MAPDEC_BATCH_PLAIN = 2
 MAPDEC_BATCH_GRAD = 4
 MAPDEC_BATCH_TIMING = 8
+MAPDEC_BATCH_SEGMENTED = 16
 PHASES = ("pack", "forward", "chains", "backward", "finalize")
 
 

@@ -33,7 +33,7 @@ def test_frame_loglik_backward_matches_oracle():
     (2.5 * ll).backward()
     ll_ref, dchan_ref, dpri_ref = oracle.loglik_grad(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps,
                                                      fr.I, fr.xmax, fr.rx, priors=fr.priors)
-    check_ll(float(ll), ll_ref)
+    check_ll(float(ll.detach()), ll_ref)
     check_grad(pri.grad.cpu().numpy(), 2.5 * dpri_ref, what="priors")
     for k in range(3):
         assert abs(float(chan.grad[k]) - 2.5 * dchan_ref[k]) <= 1e-4 * max(1.0, abs(2.5 * dchan_ref[k]))
