@@ -138,6 +138,11 @@ def _oracle_frame(args):
     return idx, fr.info_bits, time.time() - t
 
 
+# oracle cost units (3 N M q MN) one host core gets through per second, as
+# measured on the Arm host of the GPU machines; sizes the bounded samples
+ORACLE_UNITS_PER_CORE_S = 3.6e8
+
+
 def oracle_cost(q, n, N, xmax, I=2):
     M = 2 * xmax + 1
     MN = n * (I + 1) + 1
@@ -210,8 +215,9 @@ def main():
         cores = host_cores()
         per_step = []
         bits_tot = 0.0
-        budget = 1.5e9 * cores * min(args.oracle_seconds, 60.0) / max(1, steps + warmup) * 2
-        sample = oracle_sample(0, budget, 1.5e9 * 20)
+        budget = (ORACLE_UNITS_PER_CORE_S * cores * min(args.oracle_seconds, 60.0)
+                  / max(1, steps + warmup) * 2)
+        sample = oracle_sample(0, budget, ORACLE_UNITS_PER_CORE_S * 20)
         for s in range(warmup + steps):
             bits, wall = run_oracle(sample, cores)
             if s >= warmup:
@@ -237,7 +243,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        sample = oracle_sample(0, 1.2e9 * cores * args.oracle_seconds / 2, 1.2e9 * 25)
+        sample = oracle_sample(0, ORACLE_UNITS_PER_CORE_S * cores * args.oracle_seconds / 2,
+                               ORACLE_UNITS_PER_CORE_S * 25)
         bits, wall = run_oracle(sample, cores)
         cpu = {"value": bits / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{len(sample)} frames of the mixed workload in index order "
@@ -332,12 +339,18 @@ def main():
         traffic = prof.get(dom_name)
     except (OSError, ValueError):
         pass
+    try:
+        probe = mapdec.mapdec_fp32_fma_peak(stream.cuda_stream)
+    except mapdec.MapDecError:
+        probe = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak if fp32_peak else None, "traffic": traffic,
                 "kernel": f"{dom_name} phase", "phase_ms": {names[k]: round(float(phase_ms[k]), 3)
                                                              for k in range(5)},
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                               f"{sm_max:.0f} MHz"}
+                               f"{sm_max:.0f} MHz",
+                "peak_probe": probe,
+                "frac_of_probe": achieved / probe if probe else None}
     total_alg = flops["forward"] + flops["chains"] + flops["backward"]
 
     # ---- end to end through the public API with host buffers ----

@@ -271,6 +271,16 @@ int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms);
 /* Number of waves the batch's frames were split into (scratch budget). */
 int mapdec_batch_num_waves(mapdec_batch_t *b);
 
+/*
+ * Measured FP32 FMA throughput of the current device in TFLOP/s (2 flops per
+ * FMA), the arithmetic roof the decoder's kernels are reported against.  Not
+ * part of the paper's method.  Runs a short probe kernel (tens of
+ * milliseconds) on `cuda_stream` (NULL = legacy default stream) and waits for
+ * it.  Returns MAPDEC_ERR_ARG for a NULL output, MAPDEC_ERR_NOMEM or
+ * MAPDEC_ERR_CUDA on failure (the output is then 0).
+ */
+int mapdec_fp32_fma_peak(double *tflops_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,8 @@
 //   k_finalize : APPs (eq. L, normalised over D), d logP / d prior and the
 //                FP64 reduction of the channel-parameter gradient
 //                (k_grad_reduce adds the chunks of a frame in order).
+#include <cstdlib>
+
 #include "mapdec_dev.cuh"
 #include "mapdec_kernels.h"
 
@@ -40,25 +42,14 @@ __global__ void k_pack(const FrameDev *__restrict__ frames, const uint8_t *const
 }
 
 // ---------------------------------------------------------------------------
-constexpr int kChainThreads = 128;
-constexpr int kStages = 2;
+constexpr int kChainMaxThreads = 512;
+constexpr int kChainThreads = 256;  // default block size
+constexpr int kMaxStages = 8;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int w = 0; w < nw; ++w) s += red[w];  // every thread, same order: same result
-    return s;
-}
-
-// Two sums at once (normaliser and first moment).
-__device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
+// Two FP32 sums at once (row sum and first moment); every thread gets the
+// same result (the warps' partials are added in one fixed order).
+__device__ __forceinline__ void block_sum2(float a, float b, float &sa, float &sb, float *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -69,49 +60,51 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
     if (lane == 0) { red[warp] = a; red[32 + warp] = b; }
     __syncthreads();
     const int nw = (blockDim.x + 31) >> 5;
-    double sa = 0.0, sb = 0.0;
-    for (int w = 0; w < nw; ++w) { sa += red[w]; sb += red[32 + w]; }
-    a = sa;
-    b = sb;
+    float x = 0.f, y = 0.f;
+    for (int w = 0; w < nw; ++w) { x += red[w]; y += red[32 + w]; }
+    sa = x;
+    sb = y;
 }
 
 // Tilt controller (see k_chain).
-constexpr double kTiltGainMin = 0.02;  // long-run smoothing of the entropy-rate estimate
-constexpr double kTiltStepMax = 0.02;  // largest change of the tilt between two rows
-constexpr double kTiltMin = 0.2, kTiltMax = 1.6;
+constexpr float kTiltGainMin = 0.02f;  // long-run smoothing of the entropy-rate estimate
+constexpr float kTiltStepMax = 0.02f;  // largest change of the tilt between two rows
+constexpr float kTiltMin = 0.2f, kTiltMax = 1.6f;
 constexpr int kTiltEvery = 4;    // steps between tilt updates once settled
 constexpr int kTiltSettle = 64;  // updates every step for the first steps
 
-// Geometry of chunk k of the step that consumes W_i.
-struct ChunkGeom {
-    int d0, d1;     // owned states (alpha: destinations, beta: sources)
-    int r0, r1;     // W rows staged
-    int shift;      // floats between the aligned copy start and row r0
-    uint32_t bytes; // copy size
-    const float *src;
+// Geometry of chunk k of a step: the same for every symbol, relative to the
+// symbol's block of W (blocks are 16-byte aligned, so the aligned copy start,
+// the shift to row r0 and the copy size do not depend on the symbol).
+constexpr int kMaxChunks = 64;
+struct ChunkTab {
+    int d0[kMaxChunks], d1[kMaxChunks];  // owned states (alpha: destinations, beta: sources)
+    int r0[kMaxChunks], r1[kMaxChunks];  // W rows staged
+    int shift[kMaxChunks];               // floats between the aligned copy start and row r0
+    int off[kMaxChunks];                 // aligned copy start within the symbol's block (floats)
+    uint32_t bytes[kMaxChunks];          // copy size
 };
 
-__device__ __forceinline__ ChunkGeom chunk_geom(const FrameDev &f, int dir, int i, int k) {
-    ChunkGeom g;
+__device__ __forceinline__ void chunk_geom(const FrameDev &f, int dir, int k, ChunkTab &t) {
     const int CD = f.chainCD, M = f.M;
-    g.d0 = k * CD;
-    g.d1 = min(M, g.d0 + CD);
+    const int d0 = k * CD, d1 = min(M, d0 + CD);
+    int r0, r1;
     if (dir == 0) {  // destination s gets sources s - nI .. s + n
-        g.r0 = max(0, g.d0 - f.n * f.I);
-        g.r1 = min(M, g.d1 + f.n);
+        r0 = max(0, d0 - f.n * f.I);
+        r1 = min(M, d1 + f.n);
     } else {
-        g.r0 = g.d0;
-        g.r1 = g.d1;
+        r0 = d0;
+        r1 = d1;
     }
-    const long long o0 = (long long)i * f.wblk + (long long)g.r0 * f.MNS;
-    const long long o1 = (long long)i * f.wblk + (long long)g.r1 * f.MNS;
-    const long long a0 = o0 & ~3ll;
-    const long long a1 = (o1 + 3) & ~3ll;
-    g.shift = (int)(o0 - a0);
-    g.bytes = (uint32_t)((a1 - a0) * 4);
-    if (g.bytes == 0) g.bytes = 16;
-    g.src = f.W + a0;
-    return g;
+    const int o0 = r0 * f.MNS, o1 = r1 * f.MNS;
+    const int a0 = o0 & ~3, a1 = (o1 + 3) & ~3;
+    t.d0[k] = d0;
+    t.d1[k] = d1;
+    t.r0[k] = r0;
+    t.r1[k] = r1;
+    t.shift[k] = o0 - a0;
+    t.off[k] = a0;
+    t.bytes[k] = a1 > a0 ? (uint32_t)(a1 - a0) * 4u : 16u;
 }
 
 // Exponential tilt.  The forward metric alpha_i(m) is the joint probability of
@@ -120,17 +113,24 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const FrameDev &f, int dir, int 
 // posterior; the backward metric rises the same way.  Far apart in FP32, the
 // entries that carry the posterior would underflow.  The chains therefore store
 //   alpha^_i(m) = alpha_i(m) 2^{theta_i L} / Z_i,   beta^_i(m) = beta_i(m) 2^{-theta'_i L} / Y_i
-// with tilts theta driven toward h by the normalisers: with a tilt theta a
-// step's normaliser is about 2^{(theta - h) n}, so theta_{i+1} = theta_i -
-// g log2(c_i) / n (g = 1/(steps+1), floored at kTiltGainMin); after the first
-// kTiltSettle steps it is updated every kTiltEvery steps from the mean log2 c of
-// the steps since.  The producers
-// already weight every received bit by 2 (theta = 1), so a step multiplies the
-// transition sums by 2^{(theta - 1) j} (j = received length) and pre-scales
-// the source row by 2^{(theta_{i+1} - theta_i)(m - mean)}; Z_i and the tilts
-// are kept exactly in FP64, and log P(Y) = log alpha^_N(rho - tau) + log Z_N
-// - theta_N rho log 2.  The APP producer applies the matching exact factor.
-__global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restrict__ frames,
+// with tilts theta driven toward h by the row sums: with a tilt theta a step
+// grows the row sum by about 2^{(theta - h) n}, so theta_{i+1} = theta_i -
+// g log2(growth) / n (g = 1/(steps+1), floored at kTiltGainMin); after the
+// first kTiltSettle steps it is updated every kTiltEvery steps from the mean
+// growth of the steps since.  The producers already weight every received bit
+// by 2 (theta = 1), so a step multiplies the transition sums by
+// 2^{(theta - 1) j} (j = received length) and pre-scales the source row by
+// 2^{(theta_{i+1} - theta_i)(m - mean)}.  Each new row is divided by the
+// power of two 2^e just below its sum c (exact; the row then sums to [1, 2)),
+// so Z_i is a power of two times the tilt factors, kept exactly in FP64, and
+// log P(Y) = log alpha^_N(rho - tau) + log Z_N - theta_N rho log 2.  The APP
+// producer applies the matching exact factor; the per-row constants cancel in
+// the APPs and in the gradient.
+//
+// The W rows of a step stream into shared memory in chunks of chainCD states
+// (plus the band halo in the forward direction) by 1-D bulk copies completed
+// on mbarriers, chainStages chunks in flight; every wait is bounded.
+__global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__restrict__ frames,
                                                          const Work *__restrict__ work) {
     const Work wk = work[blockIdx.x];
     const FrameDev &f = frames[wk.frame];
@@ -139,17 +139,19 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
     const long long rho = f.rho;
     const int CD = f.chainCD;
     const int nck = (M + CD - 1) / CD;
+    const int NST = f.chainStages;
     const int i0 = f.seg_i0, i1 = f.seg_i1;  // symbols of this launch (segment)
-    const long long total = (long long)(i1 - i0) * nck;
     const int send = (int)(rho - (long long)n * N) + xmax;  // state of the end drift
     const bool segm = (f.chain_flags & CH_SEGMENTED) != 0;
     const bool replay = dir == 0 && (wk.tile & 2) != 0;
     // first launch of this direction: the frame boundary; otherwise the row carried over
     const bool fresh = dir == 0 ? (i0 == 0) : (i1 == N);
 
-    __shared__ uint64_t bar[kStages];
-    __shared__ double red[64];
+    __shared__ uint64_t bar[kMaxStages];
+    __shared__ float red[64];
     __shared__ int s_fail;
+    __shared__ float s_th[3];  // tilt of the current row, of the row being built, row mean
+    __shared__ float vfac[kMaxMN];
     extern __shared__ float4 sm4[];
     float *cur = reinterpret_cast<float *>(sm4);
     float *nxt = cur + Mp;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
     }
     if (threadIdx.x == 0) {
         s_fail = 0;
-        for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+        for (int st = 0; st < NST; ++st) mbar_init(&bar[st], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -173,51 +175,59 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
         float *row0 = (dir == 0) ? f.alpha + (size_t)i0 * Mp : f.beta + (size_t)i1 * Mp;
         for (int s = threadIdx.x; s < Mp; s += blockDim.x) row0[s] = cur[s];
     }
-    auto step_symbol = [&](long long g) -> int {
-        const int st = (int)(g / nck);
-        return dir == 0 ? i0 + st : i1 - 1 - st;
-    };
-    // Self-check of every copy: source inside this frame's W, destination inside
-    // its stage, 16-byte alignment and size.  A violation records ST_ARG in the
-    // frame status and completes the stage's phase with a plain arrive instead.
-    const float *wlo = f.W + (size_t)i0 * f.wblk;
-    const float *whi = f.W + (size_t)i1 * f.wblk + 16;
-    auto issue = [&](long long g) {
-        const int i = step_symbol(g);
-        const int k = (int)(g % nck);
-        const ChunkGeom cg = chunk_geom(f, dir, i, k);
-        uint64_t *b = &bar[g % kStages];
-        float *dst = stage0 + (size_t)(g % kStages) * stageFloats;
-        const bool ok = cg.src >= wlo && cg.src + cg.bytes / 4 <= whi &&
-                        cg.bytes % 16 == 0 && cg.bytes / 4 <= stageFloats &&
-                        ((uintptr_t)cg.src & 15) == 0 && ((uintptr_t)dst & 15) == 0;
-        if (ok) {
-            mbar_expect_tx(b, cg.bytes);
-            bulk_g2s(dst, cg.src, cg.bytes, b);
-        } else {
-            atomicMax(f.status, ST_ARG);
-            mbar_arrive(b);
-        }
+    auto symbol_of = [&](int st) { return dir == 0 ? i0 + st : i1 - 1 - st; };
+    // Chunk table, and a self-check of every copy it implies: source inside
+    // this launch's symbols of W (plus the 16-float tail slack), destination
+    // inside its stage, 16-byte alignment and size.  A violation records
+    // ST_ARG and the chain does not start.
+    __shared__ ChunkTab tab;
+    for (int k = threadIdx.x; k < nck && k < kMaxChunks; k += blockDim.x) {
+        chunk_geom(f, dir, k, tab);
+        const bool ok = tab.off[k] + (long long)tab.bytes[k] / 4 <= f.wblk + 16 &&
+                        tab.bytes[k] % 16 == 0 && tab.bytes[k] / 4 <= stageFloats;
+        if (!ok) atomicExch(&s_fail, ST_ARG);
+    }
+    if (threadIdx.x == 0 && (nck > kMaxChunks || ((uintptr_t)f.W & 15) != 0 || (f.wblk & 3) != 0 ||
+                             ((uintptr_t)stage0 & 15) != 0 || (stageFloats & 3) != 0))
+        atomicExch(&s_fail, ST_ARG);
+    __syncthreads();
+    if (s_fail) {  // same in every thread (read after the barrier); nothing issued yet
+        if (threadIdx.x == 0) atomicMax(f.status, s_fail);
+        return;
+    }
+    const long long total = (long long)(i1 - i0) * nck;
+    // thread 0's issue cursor: chunks issued so far, and the next one's place
+    long long issued = 0;
+    int is_st = 0, is_k = 0, is_slot = 0;
+    auto issue_next = [&]() {
+        const float *src = f.W + (size_t)symbol_of(is_st) * f.wblk + tab.off[is_k];
+        uint64_t *b = &bar[is_slot];
+        mbar_expect_tx(b, tab.bytes[is_k]);
+        bulk_g2s(stage0 + (size_t)is_slot * stageFloats, src, tab.bytes[is_k], b);
+        ++issued;
+        if (++is_k == nck) { is_k = 0; ++is_st; }
+        if (++is_slot == NST) is_slot = 0;
     };
     if (threadIdx.x == 0)
-        for (long long g = 0; g < kStages && g < total; ++g) issue(g);
+        while (issued < NST && issued < total) issue_next();
 
-    __shared__ double s_th[3];  // tilt of the current row, of the row being built, row mean
-    __shared__ float vfac[kMaxMN];
-    double logZ = 0.0;       // thread 0: log Z_i (forward) in nats
-    double theta = 1.0;      // thread 0: tilt of the current row
-    double mean = (dir == 0) ? 0.0 : (double)(send - xmax);  // thread 0: mean drift of it
-    double lc_prev = 0.0;    // thread 0: sum of log2 c since the last tilt update
-    int lc_cnt = 0;          // thread 0: number of steps in lc_prev
-    long long steps = 0;     // every thread: steps taken in this direction so far
+    // controller state (thread 0); log Z in FP64
+    double logZ = 0.0;
+    float theta = 1.f;                                    // tilt of the current row
+    float mean = (dir == 0) ? 0.f : (float)(send - xmax);  // its mean drift
+    float lrow = 0.f;      // log2 of the current row's sum
+    float lc_prev = 0.f;   // sum of log2 growth since the last tilt update
+    int lc_cnt = 0;        // number of steps in lc_prev
+    int steps = 0;         // every thread: steps taken in this direction so far
     if (!fresh && segm) {
         const ChainState &cs = f.cst[dir];
-        steps = cs.steps;
+        steps = (int)cs.steps;
         if (threadIdx.x == 0) {
-            theta = cs.theta;
-            mean = cs.mean;
+            theta = (float)cs.theta;
+            mean = (float)cs.mean;
             logZ = cs.logZ;
-            lc_prev = cs.lc_sum;
+            lc_prev = (float)cs.lc_sum;
+            lrow = (float)cs.lrow;
             lc_cnt = cs.lc_cnt;
         }
     }
@@ -226,7 +236,8 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
         if (dir == 0) { f.thf[0] = 1.0; f.mcf[0] = 0.0; }
         else f.thb[N] = 1.0;
     }
-    double part = 0.0, partm = 0.0;  // this thread's share of the normaliser and first moment
+    // this thread's share of the row sum and of its first moment
+    float part = 0.f, partm = 0.f;
     float th_cur = 1.f, th_new = 1.f, mc = 0.f;
     if (!fresh && segm && !replay) {
         // continuing a recursion: the first step here need not be an update
@@ -237,43 +248,44 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
             s_th[2] = mean;
         }
         __syncthreads();
-        th_cur = th_new = (float)s_th[0];
-        mc = (float)s_th[2];
+        th_cur = th_new = s_th[0];
+        mc = s_th[2];
         for (int j = threadIdx.x; j < MN; j += blockDim.x) vfac[j] = exp2f((th_cur - 1.f) * (float)j);
         __syncthreads();
     }
     bool failed = false;
     long long gfail = 0;
+    int st = 0, k = 0, slot = 0;
+    uint32_t ph = 0;
     for (long long g = 0; g < total; ++g) {
-        const int i = step_symbol(g);
-        const int k = (int)(g % nck);
-        const bool update = replay || steps < kTiltSettle || (steps % kTiltEvery) == 0;
+        const int i = symbol_of(st);
+        const bool update = replay || steps < kTiltSettle || (steps & (kTiltEvery - 1)) == 0;
         if (k == 0 && update) {
             // start of an update step: choose the tilt of the rows from here on
             // (the recompute sweep replays the tilts recorded by the first sweep)
             if (threadIdx.x == 0 && replay) {
-                s_th[0] = f.thf[i];
-                s_th[1] = f.thf[i + 1];
-                s_th[2] = f.mcf[i];
+                s_th[0] = (float)f.thf[i];
+                s_th[1] = (float)f.thf[i + 1];
+                s_th[2] = (float)f.mcf[i];
             } else if (threadIdx.x == 0) {
-                double tn = theta;
+                float tn = theta;
                 if (steps > 0 && lc_cnt > 0) {
-                    const double gain =
-                        fmin(1.0, fmax(kTiltGainMin, (double)lc_cnt / (double)(steps + 1)));
-                    const double d =
-                        fmin(kTiltStepMax, fmax(-kTiltStepMax, -gain * (lc_prev / lc_cnt) / n));
-                    tn = fmin(kTiltMax, fmax(kTiltMin, theta + d));
+                    const float gain =
+                        fminf(1.f, fmaxf(kTiltGainMin, (float)lc_cnt / (float)(steps + 1)));
+                    const float d = fminf(kTiltStepMax,
+                                          fmaxf(-kTiltStepMax, -gain * (lc_prev / (float)lc_cnt) / (float)n));
+                    tn = fminf(kTiltMax, fmaxf(kTiltMin, theta + d));
                 }
                 s_th[0] = theta;
                 s_th[1] = tn;
                 s_th[2] = mean;
-                lc_prev = 0.0;
+                lc_prev = 0.f;
                 lc_cnt = 0;
             }
             __syncthreads();
-            th_cur = (float)s_th[0];
-            th_new = (float)s_th[1];
-            mc = (float)s_th[2];
+            th_cur = s_th[0];
+            th_new = s_th[1];
+            mc = s_th[2];
             // forward: transition weight 2^{(theta_{i+1}-1) j}; backward: 2^{(theta'_{i+1}-1) j}
             const float phi = (dir == 0 ? th_new : th_cur) - 1.f;
             for (int j = threadIdx.x; j < MN; j += blockDim.x) vfac[j] = exp2f(phi * (float)j);
@@ -295,70 +307,107 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
             }
             th_cur = th_new;
         }
-        const ChunkGeom cg = chunk_geom(f, dir, i, k);
-        const float *buf = stage0 + (size_t)(g % kStages) * stageFloats + cg.shift;
-        if (!mbar_wait(&bar[g % kStages], (uint32_t)((g / kStages) & 1), kWaitLimit)) {
-            atomicExch(&s_fail, ST_TIMEOUT);
-        }
+        const int cd0 = tab.d0[k], cd1 = tab.d1[k], cr0 = tab.r0[k], cr1 = tab.r1[k];
+        const float *buf = stage0 + (size_t)slot * stageFloats + tab.shift[k];
+        if (!mbar_wait(&bar[slot], ph, kWaitLimit)) atomicExch(&s_fail, ST_TIMEOUT);
         // valid source rows: window start p = n i + s - xmax inside [0, rho]
-        const int vlo = max(0, (int)max(0ll, (long long)xmax - (long long)n * i));
+        const int vlo = max(0, xmax - n * i);
         const long long vhi_l = rho - (long long)n * i + xmax;
         const int vhi = (int)min((long long)M - 1, vhi_l);
-        if (dir == 0) {
-            const int lo = max(cg.r0, vlo), hi = min(cg.r1 - 1, vhi);
-            for (int s = cg.d0 + threadIdx.x; s < cg.d1; s += blockDim.x) {
-                float acc = 0.f;
-                const int jlo = max(0, s + n - hi), jhi = min(MN - 1, s + n - lo);
-                for (int j = jlo; j <= jhi; ++j) {
-                    const int src = s - j + n;
-                    acc = fmaf(cur[src], buf[(size_t)(src - cg.r0) * MNS + j] * vfac[j], acc);
-                }
-                nxt[s] = acc;
-                part += (double)acc;
-                partm += (double)acc * (double)(s - xmax);
-            }
-        } else {
-            const float dth = th_cur - th_new;  // post-scale 2^{(theta'_{i+1} - theta'_i)(m - mean)}
-            for (int s = cg.d0 + threadIdx.x; s < cg.d1; s += blockDim.x) {
-                float acc = 0.f;
-                if (s >= vlo && s <= vhi) {
+        // JS lanes share one state, each summing every JS-th term with four
+        // accumulators; the lanes combine by shuffles in a fixed order.
+        const int nst = cd1 - cd0;
+        int JS = 1;
+        while (JS < 8 && nst * JS * 2 <= (int)blockDim.x) JS *= 2;
+        const int lgJS = JS == 1 ? 0 : (JS == 2 ? 1 : (JS == 4 ? 2 : 3));
+        const int lo = max(cr0, vlo), hi = min(cr1 - 1, vhi);
+        for (int w0 = 0; w0 < nst * JS; w0 += blockDim.x) {
+            const int w = w0 + (int)threadIdx.x;
+            const int s = cd0 + (w >> lgJS), js = w & (JS - 1);
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            if (w < nst * JS) {
+                if (dir == 0) {
+                    // alpha'(s) = sum_j alpha(s - j + n) W[s - j + n][j] vfac[j]
+                    const int jlo = max(0, s + n - hi), jhi = min(MN - 1, s + n - lo);
+                    const float *cp = cur + (s + n);
+                    const float *bp = buf + (size_t)(s + n - cr0) * MNS;
+                    const int dm = MNS - 1;
+                    int j = jlo + js;
+                    for (; j + 3 * JS <= jhi; j += 4 * JS) {
+                        const int j1 = j + JS, j2 = j + 2 * JS, j3 = j + 3 * JS;
+                        a0 = fmaf(cp[-j], bp[-j * dm] * vfac[j], a0);
+                        a1 = fmaf(cp[-j1], bp[-j1 * dm] * vfac[j1], a1);
+                        a2 = fmaf(cp[-j2], bp[-j2 * dm] * vfac[j2], a2);
+                        a3 = fmaf(cp[-j3], bp[-j3 * dm] * vfac[j3], a3);
+                    }
+                    for (; j <= jhi; j += JS) a0 = fmaf(cp[-j], bp[-j * dm] * vfac[j], a0);
+                } else if (s >= vlo && s <= vhi) {
+                    // beta'(s) = sum_j W[s][j] vfac[j] beta(s + j - n)
                     const int jlo = max(0, n - s), jhi = min(MN - 1, M - 1 - s + n);
-                    const float *w = buf + (size_t)(s - cg.r0) * MNS;
-                    for (int j = jlo; j <= jhi; ++j)
-                        acc = fmaf(w[j] * vfac[j], cur[s + j - n], acc);
+                    const float *wr = buf + (size_t)(s - cr0) * MNS;
+                    const float *cq = cur + (s - n);
+                    int j = jlo + js;
+                    for (; j + 3 * JS <= jhi; j += 4 * JS) {
+                        const int j1 = j + JS, j2 = j + 2 * JS, j3 = j + 3 * JS;
+                        a0 = fmaf(wr[j] * vfac[j], cq[j], a0);
+                        a1 = fmaf(wr[j1] * vfac[j1], cq[j1], a1);
+                        a2 = fmaf(wr[j2] * vfac[j2], cq[j2], a2);
+                        a3 = fmaf(wr[j3] * vfac[j3], cq[j3], a3);
+                    }
+                    for (; j <= jhi; j += JS) a0 = fmaf(wr[j] * vfac[j], cq[j], a0);
+                }
+            }
+            float acc = (a0 + a1) + (a2 + a3);
+            for (int o = 1; o < JS; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (w < nst * JS && js == 0) {
+                if (dir == 1) {
+                    // post-scale 2^{(theta'_{i+1} - theta'_i)(m - mean)}
+                    const float dth = th_cur - th_new;
                     if (dth != 0.f) acc *= exp2f(dth * ((float)(s - xmax) - mc));
                 }
                 nxt[s] = acc;
-                part += (double)acc;
-                partm += (double)acc * (double)(s - xmax);
+                part += acc;
+                partm = fmaf(acc, (float)(s - xmax), partm);
             }
         }
         __syncthreads();  // stage consumed by everyone
-        if (threadIdx.x == 0 && g + kStages < total) issue(g + kStages);
+        if (s_fail) {     // a wait gave up (written before the barrier: same in every thread)
+            failed = true;
+            gfail = g;    // chunks g .. issued-1 may still be in flight
+            break;
+        }
+        if (threadIdx.x == 0 && issued < total) issue_next();
         if (k == nck - 1) {
-            // end of a step: normalise, keep the FP64 record
-            double c = part, cm = partm;
-            block_sum2(c, cm, red);
-            part = 0.0;
-            partm = 0.0;
-            if (!(c > 0.0) || !isfinite(c)) {
-                if (threadIdx.x == 0) atomicCAS(&s_fail, 0, ST_ZERO);
+            // end of a step: scale by a power of two, keep the exact record
+            float c, cm;
+            block_sum2(part, partm, c, cm, red);
+            part = 0.f;
+            partm = 0.f;
+            const bool bad = !(c >= 1.2e-38f) || !(c <= 3.0e38f);  // same in every thread
+            if (bad) {
+                if (threadIdx.x == 0) s_fail = ST_ZERO;
+                failed = true;
+                gfail = g + 1;
+                break;
             }
-            __syncthreads();
-            if (s_fail) { failed = true; gfail = g; break; }
-            const float inv = (float)(1.0 / c);
+            int ex;
+            frexpf(c, &ex);  // c = m 2^ex, m in [0.5, 1)
+            const float inv = ldexpf(1.f, 1 - ex);
             if (threadIdx.x == 0) {
-                const double dth = (double)th_new - (double)th_cur;
+                const float lc = log2f(c);
                 if (dir == 0 && !replay) {
-                    logZ += log(c) + dth * ((double)n * i + (double)mc) * 0.6931471805599453;
+                    logZ += ((double)(ex - 1) +
+                             (double)(th_new - th_cur) * ((double)n * i + (double)mc)) *
+                            0.6931471805599453;
                     f.thf[i + 1] = (double)th_new;
-                    f.mcf[i + 1] = cm / c;
+                    f.mcf[i + 1] = (double)(cm / c);
                 } else if (dir == 1) {
                     f.thb[i] = (double)th_new;
                 }
-                theta = (double)th_new;
+                theta = th_new;
                 mean = cm / c;
-                lc_prev += log2(c);
+                lc_prev += lc - lrow;
+                lrow = lc - (float)(ex - 1);
                 ++lc_cnt;
             }
             ++steps;
@@ -370,13 +419,16 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
             }
             __syncthreads();
         }
+        if (++k == nck) { k = 0; ++st; }
+        if (++slot == NST) { slot = 0; ph ^= 1u; }
     }
     if (failed) {
-        // Copies already issued (chunks g+1 .. g+kStages) must land before the
+        // Copies already issued (chunks gfail .. issued-1) must land before the
         // CTA's shared memory is released: wait for them, again with a bound.
+        __syncthreads();
         if (threadIdx.x == 0) {
-            for (long long h = gfail + 1; h <= gfail + kStages && h < total; ++h)
-                mbar_wait(&bar[h % kStages], (uint32_t)((h / kStages) & 1), kWaitLimit);
+            for (long long h = gfail; h < issued; ++h)
+                mbar_wait(&bar[h % NST], (uint32_t)((h / NST) & 1), kWaitLimit);
             atomicMax(f.status, s_fail);
         }
         __syncthreads();
@@ -392,6 +444,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
             cs.mean = mean;
             cs.logZ = logZ;
             cs.lc_sum = lc_prev;
+            cs.lrow = lrow;
             cs.lc_cnt = lc_cnt;
             cs.steps = steps;
         }
@@ -401,7 +454,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const FrameDev *__restr
         if (!(aN > 0.f)) {
             atomicMax(f.status, ST_ZERO);
         } else {
-            *f.loglik = log((double)aN) + logZ - theta * (double)rho * 0.6931471805599453;
+            *f.loglik = log((double)aN) + logZ - (double)theta * (double)rho * 0.6931471805599453;
         }
     }
 }
@@ -431,7 +484,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
     const FrameDev &f = frames[wk.frame];
     __shared__ double red[3][32];
     if (*f.status != ST_OK) return;
-    const int q = f.q, n = f.n, N = f.N, xmax = f.xmax;
+    const int q = f.q, n = f.n, xmax = f.xmax;
     const long long P2 = (long long)f.P * f.nsub;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
@@ -546,11 +599,11 @@ cudaError_t launch_pack(const FrameDev *frames, const uint8_t *const *rx_bytes,
 
 size_t chain_smem_bytes(const FrameDev &f) {
     const size_t stageFloats = ((size_t)(f.chainCD + f.MN + 1) * f.MNS + 8 + 3) & ~(size_t)3;
-    return 4 * (2 * (size_t)f.Mp + kStages * stageFloats);
+    return 4 * (2 * (size_t)f.Mp + (size_t)f.chainStages * stageFloats);
 }
 
 cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, size_t smem,
-                         cudaStream_t st) {
+                         int threads, cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
     // Raise the opt-in limit once to the device maximum: graphs hold chain launches
     // of several waves with different sizes, and every one must stay valid.
@@ -570,7 +623,8 @@ cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, si
         max_dyn = lim;
     }
     if ((long long)smem > max_dyn) return cudaErrorInvalidValue;
-    k_chain<<<nwork, kChainThreads, smem, st>>>(frames, work);
+    if (threads != 128 && threads != 256 && threads != 512) threads = kChainThreads;
+    k_chain<<<nwork, threads, smem, st>>>(frames, work);
     return cudaGetLastError();
 }
 

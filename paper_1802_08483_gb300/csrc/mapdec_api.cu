@@ -108,7 +108,8 @@ constexpr int kPhases = 5;  // pack, forward producers, chains, backward produce
 constexpr int kRegions = 3; // rotating scratch regions when frames need several waves
 constexpr size_t kFwdSmemBudget = 110 * 1024;
 constexpr size_t kBwdSmemBudget = 110 * 1024;  // two CTAs per SM
-constexpr size_t kChainSmemBudget = 48 * 1024;
+constexpr size_t kChainSmemBudget = 100 * 1024;  // two chains per SM
+constexpr int kChainStages = 2;
 
 struct FrameHost {
     mapdec_frame_desc_t d;
@@ -195,26 +196,43 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     }
     f.T = (int)((f.rho + 1 + P - 1) / P);
     f.T2 = (f.T + f.nsub - 1) / f.nsub;
-    // chain chunk: all states at once if it fits, else the largest power of two
-    int CD = f.M;
-    auto chain_fits = [&](int cd) {
+    // chain chunk: all states at once if it fits, else the largest power of two;
+    // as many stages in flight as the budget allows (at least two)
+    size_t cbud = kChainSmemBudget;
+    if (const char *e = std::getenv("MAPDEC_CHAIN_BUDGET_KB")) {  // tuning override
+        const int kb = std::atoi(e);
+        if (kb >= 16 && kb <= 220) cbud = (size_t)kb * 1024;
+    }
+    int stages = kChainStages;
+    if (const char *e = std::getenv("MAPDEC_CHAIN_STAGES")) {  // tuning override
+        const int v = std::atoi(e);
+        if (v >= 2 && v <= 8) stages = v;
+    }
+    auto chain_fits = [&](int cd, int stg) {
         FrameDev t = f;
         t.chainCD = cd;
-        return chain_smem_bytes(t) <= kChainSmemBudget;
+        t.chainStages = stg;
+        return chain_smem_bytes(t) <= cbud;
     };
-    if (!chain_fits(CD)) {
-        CD = 1024;
-        while (CD > 32 && !chain_fits(CD)) CD /= 2;
+    // the fewest chunks per step that fit, equal in size (at most 64 chunks)
+    int CD = f.M;
+    for (int nck = 1; nck <= 64; ++nck) {
+        CD = (f.M + nck - 1) / nck;
+        if (chain_fits(CD, stages)) break;
     }
     if (const char *e = std::getenv("MAPDEC_CHAIN_CD")) {  // tuning / testing override
         const int cd = std::atoi(e);
         if (cd >= 32) {
             FrameDev t = f;
             t.chainCD = std::min(cd, f.M);
+            t.chainStages = stages;
             if (chain_smem_bytes(t) <= 227 * 1024) CD = t.chainCD;
         }
     }
+    // at most 64 chunks per step (the chain's chunk table)
+    CD = std::max(CD, (f.M + 63) / 64);
     f.chainCD = CD;
+    f.chainStages = stages;
 }
 
 size_t frame_scratch_floats(const FrameDev &f, bool grad) {
@@ -322,6 +340,7 @@ struct mapdec_batch {
     int64_t launches_per_run[2] = {0, 0};
     bool timing = false;
     bool segmented = false;
+    int chain_threads = 0;  // 0: the chain kernel's default
     std::vector<cudaEvent_t> events;  // per wave and phase: begin, end
 
     void *dalloc(size_t bytes) {
@@ -528,6 +547,7 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
     // per-wave descriptors and work tables
     const bool segmented = (flags & MAPDEC_BATCH_SEGMENTED) != 0;
     b->segmented = segmented;
+    if (const char *e = std::getenv("MAPDEC_CHAIN_THREADS")) b->chain_threads = std::atoi(e);  // tuning
     for (size_t wi = 0; wi < b->waves.size(); ++wi) {
         Wave &w = b->waves[wi];
         size_t off = (wi % b->regions) * b->region_floats;
@@ -695,7 +715,7 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         // chains of wave w on the auxiliary stream
         CK(cudaStreamWaitEvent(cs, b->dep[2 * w], 0));
         mark(w, 2, 0, cs);
-        CK(launch_chain(wv.d_frames, wv.d_chain, wv.nchain, wv.smem_chain, cs));
+        CK(launch_chain(wv.d_frames, wv.d_chain, wv.nchain, wv.smem_chain, b->chain_threads, cs));
         ++launches;
         mark(w, 2, 1, cs);
         CK(cudaEventRecord(b->dep[2 * w + 1], cs));
@@ -759,7 +779,7 @@ int64_t enqueue_run_seg(mapdec_batch *b, bool grad, cudaStream_t st) {
                 CK(launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
                 ++launches;
             }
-            CK(launch_chain(sl.d_frames, sl.d_rec, sl.nrec, wv.smem_chain, st));
+            CK(launch_chain(sl.d_frames, sl.d_rec, sl.nrec, wv.smem_chain, b->chain_threads, st));
             ++launches;
         }
         mark(w, 1, 1);
@@ -773,7 +793,7 @@ int64_t enqueue_run_seg(mapdec_batch *b, bool grad, cudaStream_t st) {
                 CK(launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
                 ++launches;
             }
-            CK(launch_chain(sl.d_frames, sl.d_bw, sl.nbw, wv.smem_chain, st));
+            CK(launch_chain(sl.d_frames, sl.d_bw, sl.nbw, wv.smem_chain, b->chain_threads, st));
             ++launches;
             for (auto &c : sl.cls) {
                 if (c.nbwd == 0) continue;
@@ -1343,7 +1363,7 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
         e = launch_pack(fdev, (const uint8_t *const *)(A + o_rxp), (uint32_t *const *)(A + o_rxwp), 1,
                         nwords, s);
     if (e == cudaSuccess) e = launch_fwd(d.n, d.I, fdev, wf, f.T, fwd_smem_bytes(f), s);
-    if (e == cudaSuccess) e = launch_chain(fdev, wc, 2, chain_smem_bytes(f), s);
+    if (e == cudaSuccess) e = launch_chain(fdev, wc, 2, chain_smem_bytes(f), 0, s);
     if (e == cudaSuccess) e = launch_bwd(d.n, d.I, false, fdev, wb, f.T2, bwd_smem_bytes(f, false), s);
     if (e == cudaSuccess) e = launch_finalize(fdev, wfin, nfin, 1, 0, s);
     int status = MAPDEC_OK;

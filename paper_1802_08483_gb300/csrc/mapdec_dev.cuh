@@ -29,7 +29,7 @@ enum : int {
 
 // Chain state carried between the segment launches of a frame (segmented mode).
 struct ChainState {
-    double theta, mean, logZ, lc_sum;
+    double theta, mean, logZ, lc_sum, lrow;
     int lc_cnt;
     int pad;
     long long steps;
@@ -50,6 +50,7 @@ struct FrameDev {
     int S2;       // max symbols touched by one super-tile (rows of Lp per super-tile)
     int T2;       // backward super-tiles: ceil(T / nsub)
     int chainCD;  // destination/source states per chain chunk
+    int chainStages;  // chunks in flight (ring of bulk-copy stages), <= 8
     long long rho;
     long long wblk;  // floats per symbol block of W (M * MNS rounded up to 4)
     // FP32 lattice constants.  Every received bit carries a weight kappa: the

@@ -25,8 +25,9 @@ cudaError_t launch_pack(const FrameDev *frames, const uint8_t *const *rx_bytes,
                         uint32_t *const *rx_words, int nframes, long long max_words,
                         cudaStream_t st);
 size_t chain_smem_bytes(const FrameDev &f);
+// threads: 128, 256 or 512 (anything else selects the default, 256)
 cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, size_t smem,
-                         cudaStream_t st);
+                         int threads, cudaStream_t st);
 cudaError_t launch_finalize(const FrameDev *frames, const Work *work, int nwork, int nframes,
                             int grad, cudaStream_t st, bool reduce = true);
 size_t chain_state_bytes();

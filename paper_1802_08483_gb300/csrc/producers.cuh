@@ -170,20 +170,18 @@ __global__ void __launch_bounds__(kThreads) k_fwd(const FrameDev *__restrict__ f
 // memory, for every symbol i it touches:
 //   Lacc[i][D] = sum_{p in super-tile, j} alpha_i(s') R[p][D][j] beta_{i+1}(s'+j-n)
 //   Gacc[i][t] = sum_D prior_i(D) (the same sum with the t-th tangent of R)
-// Per sub-tile this is a GEMM  C (S x NR*DS) = AB (S x K) * Rt (K x NR*DS),
-// K = P*MN, whose A operand AB[c][il] = alpha*beta is built in chunks.
-// smem: Rt[K][CW]  (CW = NR*DS, DS = roundup4(q); column t*DS + D)
-//       Aw[S][P], Bw[S][BW] (BW = P + MN - 1), both carrying the tilt factors
-//       AB[kKC][S4] / reduction scratch
-//       Lacc[S2][q], Gacc[S2][3], Ct[3][S4][DS] (gradient mode)
+// Per sub-tile the contraction is evaluated as
+//   C[i][c] = sum_pl Aw[pl][i] * ( sum_j Bw[pl+j][i] * Rt[pl*MN+j][c] ),
+// i.e. the dense GEMM C(S x NR*DS) = AB(S x P*MN) * Rt(P*MN x NR*DS) with the
+// A operand AB = alpha (x) beta factored, so it is never materialised.
+// smem: Rt[K][CW]  (K = P*MN, CW = NR*DS, DS = roundup4(q); column t*DS + D)
+//       Aw[P][S4], Bw[BW][S4] (BW = P + MN - 1), both carrying the tilt factors
+//       symbol constants (3 x S4), Lacc[S2][q], Gacc[S2][3], Ct[3][S4][DS] (gradient)
 // ---------------------------------------------------------------------------
-constexpr int kKC = 32;  // K chunk
-
 template <int NB, int IB, bool GRAD>
-__global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ frames,
-                                                  const Work *__restrict__ work) {
+__global__ void __launch_bounds__(kThreads, GRAD ? 1 : 2) k_bwd(const FrameDev *__restrict__ frames,
+                                                     const Work *__restrict__ work) {
     constexpr int NR = GRAD ? 4 : 1;
-    constexpr int MT = 4;  // micro-tiles per thread
     const Work wk = work[blockIdx.x];
     const FrameDev &f = frames[wk.frame];
     const int n = (NB == 0) ? f.n : NB;
@@ -203,11 +201,12 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
     extern __shared__ float4 smem4[];
     float *Rt = reinterpret_cast<float *>(smem4);
     float *Aw = Rt + (size_t)K * CW;
-    float *Bw = Aw + (((size_t)f.S * P + 3) & ~(size_t)3);
-    float *AB = Bw + (((size_t)f.S * BW + 3) & ~(size_t)3);
-    size_t abn = (size_t)kKC * Smax4;
-    if (abn < (size_t)kThreads * 16) abn = (size_t)kThreads * 16;
-    float *Lacc = AB + abn;
+    float *Bw = Aw + (size_t)P * Smax4;
+    int *symE = reinterpret_cast<int *>(Bw + (size_t)BW * Smax4);  // integer part of the alpha-side exponent
+    float *symF = reinterpret_cast<float *>(symE + Smax4);      // its fraction
+    float *symG = symF + Smax4;                                 // its slope in pl
+    float *symPhi = symG + Smax4;                               // theta'_{i+1} - 1
+    float *Lacc = symPhi + Smax4;
     float *Gacc = Lacc + (((size_t)f.S2 * q + 3) & ~(size_t)3);
     float *Ct = Gacc + (((size_t)f.S2 * 3 + 3) & ~(size_t)3);
 
@@ -255,155 +254,137 @@ __global__ void __launch_bounds__(kThreads) k_bwd(const FrameDev *__restrict__ f
         // factor that undoes the chains' tilts (k_chain):
         //   sigma ~ alpha^_i(m') beta^_{i+1}(m) 2^{(theta'_{i+1} - theta_i)(m' - mean_i)}
         //           2^{(theta'_{i+1} - 1) j} prior R~
-        // up to a constant per symbol.  The alpha-side factor is applied in log
-        // space and clamped, so a zero alpha never meets an overflowing factor.
-        // The per-j factor 2^{phi j}, phi = theta'_{i+1} - 1, splits exactly as
-        // 2^{phi (pl + j)} 2^{-phi pl}: folded into the beta window (index pl + j)
-        // and the alpha window (index pl).
-        for (int idx = threadIdx.x; idx < S * P; idx += blockDim.x) {
-            const int il = idx / P, pl = idx - il * P;
+        // up to a constant per symbol.  The per-j factor 2^{phi j}, phi =
+        // theta'_{i+1} - 1, splits exactly as 2^{phi (pl + j)} 2^{-phi pl}: folded
+        // into the beta window (index pl + j) and the alpha window (index pl).
+        // With m' = p0 + pl - n i the alpha-side exponent is e0_i + g_i pl,
+        // e0_i = (theta'_{i+1} - theta_i)(p0 - n i - mean_i) (FP64, split into
+        // integer and fraction), g_i = theta'_{i+1} - theta_i - phi; the factor
+        // is applied as alpha 2^frac scaled by 2^int (exact), clamped below
+        // overflow.
+        for (int il = threadIdx.x; il < S4; il += blockDim.x) {
+            int ei = 0;
+            float ef = 0.f, g = 0.f, phi = 0.f;
+            if (il < S) {
+                const long long i = ilo + il;
+                const double dth = f.thb[i + 1] - f.thf[i];
+                const double ph = f.thb[i + 1] - 1.0;
+                const double e0 = dth * ((double)(p0 - (long long)n * i) - f.mcf[i]);
+                const double r = rint(e0);
+                ei = (int)fmax(-100000.0, fmin(100000.0, r));
+                ef = (float)(e0 - r);
+                g = (float)(dth - ph);
+                phi = (float)ph;
+            }
+            symE[il] = ei;
+            symF[il] = ef;
+            symG[il] = g;
+            symPhi[il] = phi;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < P * S4; idx += blockDim.x) {
+            const int pl = idx / S4, il = idx - pl * S4;
             const long long i = ilo + il, p = p0 + pl;
             const long long s = p - (long long)n * i + xmax;
             float v = 0.f;
-            if (s >= 0 && s < M && p <= rho) {
+            if (il < S && s >= 0 && s < M && p <= rho) {
                 const float a = f.alpha[(size_t)i * f.Mp + s];
                 if (a > 0.f) {
-                    const double phi = f.thb[i + 1] - 1.0;
-                    const float e = (float)((f.thb[i + 1] - f.thf[i]) *
-                                                ((double)(s - xmax) - f.mcf[i]) -
-                                            phi * (double)pl);
-                    v = exp2f(fminf(log2f(a) + e, 126.f));
+                    const float e = fmaf(symG[il], (float)pl, symF[il]);
+                    const float k = rintf(e);
+                    const int ex = symE[il] + (int)k;
+                    v = a * exp2f(e - k);
+                    v = fminf(ldexpf(v, min(max(ex, -300), 300)), 3.0e38f);
                 }
             }
             Aw[idx] = v;
         }
-        for (int idx = threadIdx.x; idx < S * BW; idx += blockDim.x) {
-            const int il = idx / BW, k = idx - il * BW;
+        for (int idx = threadIdx.x; idx < BW * S4; idx += blockDim.x) {
+            const int k = idx / S4, il = idx - k * S4;
             const long long i = ilo + il;
             const long long s = p0 - (long long)n * i + xmax - n + k;
             float v = 0.f;
-            if (s >= 0 && s < M) {
+            if (il < S && s >= 0 && s < M) {
                 const float b = f.beta[(size_t)(i + 1) * f.Mp + s];
-                v = b * exp2f((float)(f.thb[i + 1] - 1.0) * (float)k);
+                v = b * exp2f(symPhi[il] * (float)k);
             }
             Bw[idx] = v;
         }
         __syncthreads();
 
-        // (C) GEMM over K in chunks.  Micro-tiles 4 rows x 4 columns; when there
-        // are fewer micro-tiles than threads the K range is split KS ways.
+        // (C) register micro-tiles of 4 symbols x 4 columns.  With fewer
+        // micro-tiles than threads, KS adjacent lanes share one micro-tile and
+        // split the positions; their partial sums combine by shuffles, in a
+        // fixed order.
         const int NRG = S4 / 4, NCG = CW / 4;
         const int NMT = NRG * NCG;
-        const int KS = NMT >= (int)blockDim.x ? 1 : (int)blockDim.x / NMT;
-        const int slots = NMT * KS;
-        const int per_pass = (int)blockDim.x * MT;
-        const int npass = (NMT + per_pass - 1) / per_pass;
-        for (int pass = 0; pass < npass; ++pass) {
-            float acc[MT][4][4];
+        int KS = 1;
+        while (KS < 32 && KS * 2 <= P && NMT * KS * 2 <= (int)blockDim.x) KS *= 2;
+        const int units = NMT * KS;
+        const float4 *Aw4 = reinterpret_cast<const float4 *>(Aw);
+        const float4 *Bw4 = reinterpret_cast<const float4 *>(Bw);
+        const float4 *Rt4 = reinterpret_cast<const float4 *>(Rt);
+        const int sr = S4 / 4, cr = CW / 4;
+        for (int u0 = 0; u0 < units; u0 += blockDim.x) {
+            const int u = u0 + (int)threadIdx.x;
+            const bool active = u < units;
+            const int mt = active ? u / KS : 0;
+            const int ks = u & (KS - 1);
+            const int rg = mt / NCG, cg = mt - rg * NCG;
+            float acc[4][4];
 #pragma unroll
-            for (int m = 0; m < MT; ++m)
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+            if (active) {
+                for (int pl = ks; pl < P; pl += KS) {
+                    const float4 a = Aw4[pl * sr + rg];
+                    if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f) continue;
+                    float t[4][4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) t[r][c] = 0.f;
+                    const float4 *bp = Bw4 + pl * sr + rg;
+                    const float4 *rp = Rt4 + (size_t)pl * MN * cr + cg;
+#pragma unroll 8
+                    for (int j = 0; j < MN; ++j) {
+                        const float4 b = bp[j * sr];
+                        const float4 rr = rp[j * cr];
+                        const float bv[4] = {b.x, b.y, b.z, b.w};
+                        const float rv[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) t[r][c] = fmaf(bv[r], rv[c], t[r][c]);
+                    }
+                    const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], t[r][c], acc[r][c]);
+                }
+            }
+            for (int o = 1; o < KS; o <<= 1) {
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) acc[m][r][u] = 0.f;
-            for (int kc0 = 0; kc0 < K; kc0 += kKC) {
-                const int kn = min(kKC, K - kc0);
-                for (int idx = threadIdx.x; idx < kn * S4; idx += blockDim.x) {
-                    const int kk = idx / S4, il = idx - kk * S4;
-                    const int c = kc0 + kk;
-                    const int pl = c / MN, j = c - pl * MN;
-                    AB[idx] = (il < S) ? Aw[il * P + pl] * Bw[il * BW + pl + j] : 0.f;
-                }
-                __syncthreads();
-                if (KS > 1) {
-                    const int t = threadIdx.x;
-                    if (t < slots) {
-                        const int mt = t % NMT, ks = t / NMT;
-                        const int rg = mt / NCG, cg = mt - rg * NCG;
-                        for (int kk = ks; kk < kn; kk += KS) {
-                            const float4 a =
-                                *reinterpret_cast<const float4 *>(AB + (size_t)kk * S4 + rg * 4);
-                            const float4 b = *reinterpret_cast<const float4 *>(
-                                Rt + (size_t)(kc0 + kk) * CW + cg * 4);
-                            const float av[4] = {a.x, a.y, a.z, a.w};
-                            const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                                for (int u = 0; u < 4; ++u)
-                                    acc[0][r][u] = fmaf(av[r], bv[u], acc[0][r][u]);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int m = 0; m < MT; ++m) {
-                        const int mt = pass * per_pass + m * (int)blockDim.x + threadIdx.x;
-                        if (mt < NMT) {
-                            const int rg = mt / NCG, cg = mt - rg * NCG;
-                            for (int kk = 0; kk < kn; ++kk) {
-                                const float4 a = *reinterpret_cast<const float4 *>(
-                                    AB + (size_t)kk * S4 + rg * 4);
-                                const float4 b = *reinterpret_cast<const float4 *>(
-                                    Rt + (size_t)(kc0 + kk) * CW + cg * 4);
-                                const float av[4] = {a.x, a.y, a.z, a.w};
-                                const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                                    for (int u = 0; u < 4; ++u)
-                                        acc[m][r][u] = fmaf(av[r], bv[u], acc[m][r][u]);
-                            }
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            if (KS > 1) {
-                float *Red = AB;
-                if ((int)threadIdx.x < slots) {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            Red[(size_t)threadIdx.x * 16 + r * 4 + u] = acc[0][r][u];
-                }
-                __syncthreads();
-                if ((int)threadIdx.x < NMT) {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            float s = 0.f;
-                            for (int ks = 0; ks < KS; ++ks)
-                                s += Red[(size_t)(ks * NMT + threadIdx.x) * 16 + r * 4 + u];
-                            acc[0][r][u] = s;
-                        }
-                }
-                __syncthreads();
+                    for (int c = 0; c < 4; ++c)
+                        acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], o);
             }
             // (D) owners add into the accumulators / stage tangent sums
-#pragma unroll
-            for (int m = 0; m < MT; ++m) {
-                int mt;
-                if (KS > 1) {
-                    if (m > 0) break;
-                    mt = (int)threadIdx.x;
-                } else {
-                    mt = pass * per_pass + m * (int)blockDim.x + threadIdx.x;
-                }
-                if (mt >= NMT) continue;
-                const int rg = mt / NCG, cg = mt - rg * NCG;
+            if (active && ks == 0) {
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int il = rg * 4 + r;
                     if (il >= S) break;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int col = cg * 4 + u;
+                    for (int c = 0; c < 4; ++c) {
+                        const int col = cg * 4 + c;
                         const int th = col / DS, D = col - th * DS;
                         if (D >= q) continue;
-                        if (th == 0) Lacc[(size_t)(off + il) * q + D] += acc[m][r][u];
-                        else Ct[((size_t)(th - 1) * Smax4 + il) * DS + D] = acc[m][r][u];
+                        if (th == 0) Lacc[(size_t)(off + il) * q + D] += acc[r][c];
+                        else Ct[((size_t)(th - 1) * Smax4 + il) * DS + D] = acc[r][c];
                     }
                 }
             }

@@ -28,10 +28,7 @@ size_t bwd_smem_bytes(const FrameDev &f, bool grad) {
     const size_t DS = ((size_t)f.q + 3) & ~(size_t)3;
     const size_t K = (size_t)f.P * f.MN;
     const size_t BW = (size_t)f.P + f.MN - 1;
-    size_t ab = (size_t)kKC * Smax4;
-    if (ab < (size_t)kThreads * 16) ab = (size_t)kThreads * 16;
-    size_t fl = K * NR * DS + ((f.S * (size_t)f.P + 3) & ~(size_t)3) +
-                ((f.S * BW + 3) & ~(size_t)3) + ab +
+    size_t fl = K * NR * DS + (size_t)f.P * Smax4 + BW * Smax4 + 4 * Smax4 +
                 (((size_t)f.S2 * f.q + 3) & ~(size_t)3) +
                 (((size_t)f.S2 * 3 + 3) & ~(size_t)3);
     if (grad) fl += 3 * Smax4 * DS;

@@ -80,6 +80,7 @@ _SIGS = {
     "mapdec_batch_last_launches": (ctypes.c_int64, [_VP]),
     "mapdec_batch_phase_ms": (ctypes.c_int, [_VP, _VP]),
     "mapdec_batch_num_waves": (ctypes.c_int, [_VP]),
+    "mapdec_fp32_fma_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _VP]),
 }
 
 
@@ -261,6 +262,13 @@ def mapdec_batch_phase_ms(b):
 
 def mapdec_batch_num_waves(b):
     return int(load().mapdec_batch_num_waves(b))
+
+
+def mapdec_fp32_fma_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(load().mapdec_fp32_fma_peak(ctypes.byref(v), _ptr(stream)), "mapdec_fp32_fma_peak")
+    return v.value
 
 
 # --------------------------------------------------------------------------

@@ -283,3 +283,13 @@ def test_error_statuses():
     # the handle stays usable after an error
     app, ll = d2.decode(np.array([0, 0, 0, 1, 1, 1], np.uint8))
     assert app[0, 0] == pytest.approx(1.0) and app[1, 1] == pytest.approx(1.0)
+
+
+def test_fp32_fma_peak_probe():
+    """The FMA probe reports a throughput between half and 105% of the
+    SM-count x 128 lanes x 2 x maximum-clock figure."""
+    import torch
+    v = mapdec.mapdec_fp32_fma_peak()
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    assert 0.5 * nominal <= v <= 1.05 * nominal, (v, nominal)
