@@ -176,6 +176,22 @@ def run_oracle(frames_idx, cores):
     return bits, wall
 
 
+PHASE_KERNELS = {"pack": "k_pack", "forward": "k_fwd, all (n, I) classes",
+                 "chains": "k_chain", "backward": "k_bwd, all (n, I) classes",
+                 "finalize": "k_finalize"}
+
+
+def kernel_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1802_08483_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -333,10 +349,13 @@ def main():
     dom_name = names[dom]
     dom_flops = flops.get(dom_name, 0)
     achieved = dom_flops / (phase_ms[dom] / 1e3) / 1e12 if phase_ms[dom] > 0 else 0.0
+    # DRAM bytes of the phase per step from the committed launch-list capture;
+    # null when the kernel sources changed since the counters were taken
     traffic = None
     try:
         prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic = prof.get(dom_name)
+        if prof.get("csrc_sha1") == kernel_sources_sha1():
+            traffic = prof.get(dom_name)
     except (OSError, ValueError):
         pass
     try:
@@ -345,7 +364,7 @@ def main():
         probe = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak if fp32_peak else None, "traffic": traffic,
-                "kernel": f"{dom_name} phase", "phase_ms": {names[k]: round(float(phase_ms[k]), 3)
+                "kernel": f"{dom_name} phase ({PHASE_KERNELS.get(dom_name, '')})", "phase_ms": {names[k]: round(float(phase_ms[k]), 3)
                                                              for k in range(5)},
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                f"{sm_max:.0f} MHz",
