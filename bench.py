@@ -26,6 +26,7 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_TUNING = os.path.join(ROOT, "paper_1802_08483_gb300", "tuning", "gb300_mixed4096.json")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -212,6 +213,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=20.0)
+    ap.add_argument("--tuning", default=DEFAULT_TUNING,
+                    help="tuning table (JSON written by paper_1802_08483_gb300.tune); '' = none")
     ap.add_argument("--mem-budget-gb", type=float, default=0.0,
                     help="device scratch budget (0 = 60%% of free memory); frames beyond it "
                          "are decoded in further waves")
@@ -277,6 +280,11 @@ def main():
     torch.cuda.set_device(local_rank)
     libbuild.build()
     mapdec.load()
+    tuning = None
+    if args.tuning and os.path.exists(args.tuning):
+        from paper_1802_08483_gb300 import tune as libtune
+        libtune.load(args.tuning)
+        tuning = os.path.relpath(args.tuning, ROOT)
 
     # ---- workload ----
     t0 = time.time()
@@ -418,6 +426,7 @@ def main():
                        "frames_per_gpu": args.frames, "info_bits_per_gpu_step": bits_per_step,
                        "l2": "inputs and scratch larger than L2 (no flush needed)",
                        "waves": mapdec.mapdec_batch_num_waves(b.b),
+                       "tuning": tuning,
                        "parallelism": f"frames sharded, {n_gpus} GPU(s), no collective",
                        "gen_seconds": round(gen_s, 1)},
             "roofline": roofline,

@@ -268,6 +268,31 @@ int64_t mapdec_batch_last_launches(mapdec_batch_t *b);
  */
 int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms);
 
+/*
+ * Tuning table (not in the paper, which picks its block sizes by a run-time
+ * rule): launch parameters per (q, n, I) class, applied to batches created
+ * afterwards (not to MAPDEC_BATCH_PLAIN batches).  A zero field keeps the
+ * planner's choice; values that do not fit the device are replaced by the
+ * planner's choice.  The table is process-wide and guarded by a mutex.
+ */
+typedef struct {
+    int P;               /* received positions per producer tile */
+    int nsub;            /* producer tiles per APP super-tile */
+    int chain_budget_kb; /* shared memory of one recursion CTA, 16..220 KB */
+    int chain_stages;    /* bulk-copy stages in flight in the recursions, 2..8 */
+    int store_metric;    /* 1: keep the receiver metrics R in device memory between the
+                            forward and APP producers (decode only; about
+                            (rho+1) * roundup4(q) * (n(I+1)+1) * 4 bytes per frame);
+                            0 or -1: recompute them */
+} mapdec_tune_t;
+
+/* Set (t != NULL) or remove (t == NULL) the entry of class (q, n, I). */
+int mapdec_tune_set(int q, int n, int I, const mapdec_tune_t *t);
+/* Copy the entry of class (q, n, I) to *t; MAPDEC_ERR_ARG if there is none. */
+int mapdec_tune_get(int q, int n, int I, mapdec_tune_t *t);
+/* Remove every entry. */
+int mapdec_tune_clear(void);
+
 /* Number of waves the batch's frames were split into (scratch budget). */
 int mapdec_batch_num_waves(mapdec_batch_t *b);
 

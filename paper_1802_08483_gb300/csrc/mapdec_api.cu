@@ -122,10 +122,39 @@ struct FrameHost {
     size_t scratch_floats = 0;
     double cost = 0.0;
     int segK = 0, nseg = 1; // segmented mode: symbols per segment, segments
+    bool store = false;     // keep the receiver metrics in HBM for the APP producer
 };
 
+// Stored receiver metrics of a frame: T tiles of P*MN rows x roundup4(q) floats.
+size_t metric_store_floats(const FrameDev &f) {
+    return (size_t)f.T * f.P * f.MN * (size_t)((f.q + 3) & ~3);
+}
+
+// Tuning table: launch parameters per (q, n, I) class, set through
+// mapdec_tune_set (normally from a tuner's measurements).  Read when a batch
+// is planned.
+struct TuneEntry {
+    int q, n, I;
+    mapdec_tune_t t;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+
+bool tune_lookup(int q, int n, int I, mapdec_tune_t &out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto &e : g_tune)
+        if (e.q == q && e.n == n && e.I == I) {
+            out = e.t;
+            return true;
+        }
+    return false;
+}
+
 // Fill shape-dependent fields of dev (P, S, T, nsub, ...) for received length rho.
-void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP) {
+// tune (may be null) holds the class's tuned parameters (0 = planner's choice);
+// forceP > 0 (testing) overrides the tile size.
+void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP,
+                const mapdec_tune_t *tune = nullptr) {
     f.q = d.q; f.n = d.n; f.N = d.N; f.I = d.I; f.xmax = d.xmax;
     f.M = 2 * d.xmax + 1;
     f.Mp = (int)rup(f.M, 4);
@@ -162,9 +191,11 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     };
     // positions per sub-tile
     static const int cand[] = {64, 48, 32, 24, 16, 12, 8, 6, 4, 2, 1};
+    const int want = forceP > 0 ? forceP : (tune && tune->P > 0 ? tune->P : 0);
     int P = 1;
+    for (int pass = want > 0 ? 0 : 1; pass < 2; ++pass)
     for (int c : cand) {
-        if (forceP > 0 && c != forceP) continue;
+        if (pass == 0 && c != want) continue;
         FrameDev t = f;
         t.P = c;
         t.S = symbols_span(c);
@@ -177,6 +208,7 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
         }
         if (bwd_smem_bytes(t, grad) > kBwdSmemBudget) continue;
         P = c;
+        pass = 2;  // found: leave both loops
         break;
     }
     f.P = P;
@@ -185,6 +217,10 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     f.S2 = symbols_span((long long)P * f.nsub);
     while (f.nsub > 1 && bwd_smem_bytes(f, grad) > kBwdSmemBudget) {
         f.nsub /= 2;
+        f.S2 = symbols_span((long long)P * f.nsub);
+    }
+    if (tune && tune->nsub > 0 && tune->nsub <= f.nsub) {
+        f.nsub = tune->nsub;
         f.S2 = symbols_span((long long)P * f.nsub);
     }
     if (const char *e = std::getenv("MAPDEC_FORCE_NSUB")) {  // testing override
@@ -199,11 +235,14 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     // chain chunk: all states at once if it fits, else the largest power of two;
     // as many stages in flight as the budget allows (at least two)
     size_t cbud = kChainSmemBudget;
+    if (tune && tune->chain_budget_kb >= 16 && tune->chain_budget_kb <= 220)
+        cbud = (size_t)tune->chain_budget_kb * 1024;
     if (const char *e = std::getenv("MAPDEC_CHAIN_BUDGET_KB")) {  // tuning override
         const int kb = std::atoi(e);
         if (kb >= 16 && kb <= 220) cbud = (size_t)kb * 1024;
     }
     int stages = kChainStages;
+    if (tune && tune->chain_stages >= 2 && tune->chain_stages <= 8) stages = tune->chain_stages;
     if (const char *e = std::getenv("MAPDEC_CHAIN_STAGES")) {  // tuning override
         const int v = std::atoi(e);
         if (v >= 2 && v <= 8) stages = v;
@@ -470,7 +509,13 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         st = pack_codebook(h.d.codebook, h.d.q, h.d.n, h.cw);
         if (st) return st;
         h.d.codebook = nullptr;
-        plan_shape(h.dev, h.d, b->grad, (flags & MAPDEC_BATCH_PLAIN) ? 0 : forceP);
+        const bool plain = (flags & MAPDEC_BATCH_PLAIN) != 0;
+        mapdec_tune_t tu{};
+        const bool tuned = !plain && tune_lookup(h.d.q, h.d.n, h.d.I, tu);
+        plan_shape(h.dev, h.d, b->grad, plain ? 0 : forceP, tuned ? &tu : nullptr);
+        h.store = tuned && tu.store_metric == 1;
+        if (const char *e = std::getenv("MAPDEC_STORE_R")) h.store = std::atoi(e) == 1;  // testing
+        if (plain || b->grad || (flags & MAPDEC_BATCH_SEGMENTED)) h.store = false;
         if (flags & MAPDEC_BATCH_SEGMENTED) {
             int K = (int)std::ceil(std::sqrt((double)h.d.N));
             if (const char *e = std::getenv("MAPDEC_SEG_K")) {  // tuning / testing override
@@ -483,6 +528,7 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             h.scratch_floats = frame_scratch_floats_seg(h.dev, K, h.nseg, b->grad);
         } else {
             h.scratch_floats = frame_scratch_floats(h.dev, b->grad);
+            if (h.store) h.scratch_floats += rup(metric_store_floats(h.dev), 64);
         }
         h.cost = frame_cost(h.dev);
         h.rx_off = b->rx_total;
@@ -575,6 +621,8 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
                 f.thb = (double *)(base + o); o += rup((size_t)(f.N + 1) * 2, 64);
                 f.Gc = nullptr;
                 if (b->grad) { f.Gc = (double *)(base + o); o += rup((size_t)finalize_chunks(f.N) * 3 * 2, 64); }
+                f.Rg = nullptr;
+                if (h.store) { f.Rg = base + o; o += rup(metric_store_floats(f), 64); }
             } else {
                 // buffers of one segment; per-segment descriptors shift their bases
                 const int K = h.segK, S = h.nseg;
@@ -1145,6 +1193,30 @@ int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms) {
 }
 
 int mapdec_batch_num_waves(mapdec_batch_t *b) { return b ? (int)b->waves.size() : -1; }
+
+int mapdec_tune_set(int q, int n, int I, const mapdec_tune_t *t) {
+    if (q < 2 || n < 1 || I < 1) return MAPDEC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (size_t k = 0; k < g_tune.size(); ++k)
+        if (g_tune[k].q == q && g_tune[k].n == n && g_tune[k].I == I) {
+            if (t) g_tune[k].t = *t;
+            else g_tune.erase(g_tune.begin() + (long)k);
+            return MAPDEC_OK;
+        }
+    if (t) g_tune.push_back({q, n, I, *t});
+    return MAPDEC_OK;
+}
+
+int mapdec_tune_get(int q, int n, int I, mapdec_tune_t *t) {
+    if (!t) return MAPDEC_ERR_ARG;
+    return tune_lookup(q, n, I, *t) ? MAPDEC_OK : MAPDEC_ERR_ARG;
+}
+
+int mapdec_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    return MAPDEC_OK;
+}
 
 // ---------------------------------------------------------------------------
 // single-frame handle

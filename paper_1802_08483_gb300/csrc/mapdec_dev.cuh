@@ -75,6 +75,8 @@ struct FrameDev {
     float *Lp;       // T2 * S2 * q  partial unnormalised APP sums per super-tile
     float *Gp;       // T2 * S2 * 3  partial tangent sums per super-tile (gradient mode)
     float *Rout;     // receiver-metric dump (debug entry), (rho+1)*q*MN or null
+    float *Rg;       // stored receiver metrics (or null: recompute), T * P*MN * DS:
+                     // tile t at t*P*MN*DS, row pl*MN + j, column D (DS = roundup4(q))
     // Exponential tilt of the stored forward/backward rows (see k_chain):
     // thf[i], mcf[i]: tilt and mean drift of forward row i; thb[i]: tilt of
     // backward row i.  N+1 doubles each.

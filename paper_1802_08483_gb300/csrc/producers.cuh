@@ -101,6 +101,16 @@ __global__ void __launch_bounds__(kThreads) k_fwd(const FrameDev *__restrict__ f
         const int D = idx / (RS - NC), c = NC + idx % (RS - NC);
         Rs[(size_t)D * RS + c] = 0.f;
     }
+    __syncthreads();
+    if (f.Rg) {
+        // keep R for the APP producer: rows pl*MN + j, columns D (zero-padded to DS)
+        const int DS = (q + 3) & ~3;
+        float *dst = f.Rg + (size_t)wk.tile * NC * DS;
+        for (int idx = threadIdx.x; idx < NC * DS; idx += blockDim.x) {
+            const int row = idx / DS, D = idx - row * DS;
+            dst[idx] = D < q ? Rs[(size_t)D * RS + row] : 0.f;
+        }
+    }
     // (B) priors of the touched symbols, transposed to [D][il]
     for (int idx = threadIdx.x; idx < S4 * q; idx += blockDim.x) {
         const int il = idx / q, D = idx - il * q;
@@ -225,7 +235,14 @@ __global__ void __launch_bounds__(kThreads, GRAD ? 1 : 2) k_bwd(const FrameDev *
         const int off = ilo - ilo2;  // row of symbol ilo in the accumulators
 
         // (A) receiver metrics (and tangents); lanes cover consecutive D for one p.
-        for (int idx = threadIdx.x; idx < P * q; idx += blockDim.x) {
+        // Decode mode with stored metrics: copy the tile's block instead.
+        if (!GRAD && f.Rg) {
+            const float4 *src = reinterpret_cast<const float4 *>(
+                f.Rg + ((size_t)wk.tile * f.nsub + sub) * (size_t)K * DS);
+            float4 *dst = reinterpret_cast<float4 *>(Rt);
+            for (int idx = threadIdx.x; idx < K * DS / 4; idx += blockDim.x) dst[idx] = __ldg(src + idx);
+        }
+        for (int idx = threadIdx.x; idx < ((!GRAD && f.Rg) ? 0 : P * q); idx += blockDim.x) {
             const int pl = idx / q, D = idx - pl * q;
             const long long p = p0 + pl;
 #pragma unroll
@@ -243,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, GRAD ? 1 : 2) k_bwd(const FrameDev *
                 for (int j = 0; j < MN; ++j) dst[(size_t)j * CW] = v[j];
             }
         }
-        if (DS > q) {
+        if (DS > q && (GRAD || !f.Rg)) {
             for (int idx = threadIdx.x; idx < K * NR * (DS - q); idx += blockDim.x) {
                 const int row = idx / (NR * (DS - q)), r2 = idx - row * (NR * (DS - q));
                 const int th = r2 / (DS - q), col = q + r2 % (DS - q);

@@ -81,7 +81,19 @@ _SIGS = {
     "mapdec_batch_phase_ms": (ctypes.c_int, [_VP, _VP]),
     "mapdec_batch_num_waves": (ctypes.c_int, [_VP]),
     "mapdec_fp32_fma_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _VP]),
+    "mapdec_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
+    "mapdec_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
+    "mapdec_tune_clear": (ctypes.c_int, []),
 }
+
+
+class Tune(ctypes.Structure):
+    """mapdec_tune_t: launch parameters of one (q, n, I) class (0 = planner's choice)."""
+    _fields_ = [("P", ctypes.c_int), ("nsub", ctypes.c_int), ("chain_budget_kb", ctypes.c_int),
+                ("chain_stages", ctypes.c_int), ("store_metric", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 def header_symbols() -> list:
@@ -262,6 +274,26 @@ def mapdec_batch_phase_ms(b):
 
 def mapdec_batch_num_waves(b):
     return int(load().mapdec_batch_num_waves(b))
+
+
+def mapdec_tune_set(q, n, I, tune=None):
+    """Set (tune: Tune or dict) or remove (None) the tuning entry of class (q, n, I)."""
+    if isinstance(tune, dict):
+        tune = Tune(**{k: int(v) for k, v in tune.items() if k in dict(Tune._fields_)})
+    _check(load().mapdec_tune_set(int(q), int(n), int(I),
+                                  ctypes.byref(tune) if tune is not None else None),
+           "mapdec_tune_set")
+
+
+def mapdec_tune_get(q, n, I):
+    """The tuning entry of class (q, n, I) as a dict, or None."""
+    t = Tune()
+    st = load().mapdec_tune_get(int(q), int(n), int(I), ctypes.byref(t))
+    return t.as_dict() if st == MAPDEC_OK else None
+
+
+def mapdec_tune_clear():
+    _check(load().mapdec_tune_clear(), "mapdec_tune_clear")
 
 
 def mapdec_fp32_fma_peak(stream=None) -> float:

@@ -1,0 +1,102 @@
+"""Stored receiver metrics and tuned launch parameters on the GPU.
+
+  * keeping R in device memory between the producers gives bit-identical
+    results to recomputing it (same lattice, same inputs);
+  * tuned parameters (tile size, super-tile depth, recursion budget and
+    stages, stored metrics) keep parity with the FP64 oracle;
+  * the tuner runs end to end on a small workload and leaves a table whose
+    batches decode to the untuned results.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from parity import check_app, check_ll
+from paper_1802_08483_gb300 import mapdec, synth, tune
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_08483_gb300 import build
+    build.build()
+    mapdec.load()
+    oracle.build()
+    yield
+    mapdec.mapdec_tune_clear()
+
+
+def _frames(count=20, maxN=700):
+    out, k = [], 0
+    while len(out) < count:
+        fr = synth.config_frame(3, k)
+        if fr.N <= maxN:
+            out.append(fr)
+        k += 1
+    return out
+
+
+def _decode(frames):
+    b = mapdec.Batch(frames, flags=mapdec.MAPDEC_BATCH_GRAPH)
+    rx, pr = b.concat_inputs()
+    st, app, ll = b.decode(rx, pr)
+    out = (st, [a.copy() for a in b.split(app)], ll.copy())
+    b.close()
+    return out
+
+
+def test_stored_metrics_bit_identical(monkeypatch):
+    mapdec.mapdec_tune_clear()
+    frames = _frames()
+    monkeypatch.setenv("MAPDEC_STORE_R", "0")
+    st0, app0, ll0 = _decode(frames)
+    monkeypatch.setenv("MAPDEC_STORE_R", "1")
+    st1, app1, ll1 = _decode(frames)
+    assert st0 == 0 and st1 == 0
+    for k in range(len(frames)):
+        assert np.array_equal(app0[k], app1[k]), k
+        assert ll0[k] == ll1[k], k
+
+
+@pytest.mark.parametrize("t", [
+    {"P": 2, "nsub": 2, "chain_budget_kb": 72, "chain_stages": 2, "store_metric": 1},
+    {"P": 16, "nsub": 4, "chain_budget_kb": 150, "chain_stages": 3, "store_metric": 0},
+    {"P": 1, "nsub": 0, "chain_budget_kb": 48, "chain_stages": 4, "store_metric": 1},
+])
+def test_tuned_parameters_keep_parity(t):
+    mapdec.mapdec_tune_clear()
+    frames = _frames(12, 500)
+    for key in tune.classes(frames):
+        mapdec.mapdec_tune_set(*key, t)
+    st, apps, ll = _decode(frames)
+    mapdec.mapdec_tune_clear()
+    assert st == 0, mapdec.mapdec_strerror(st)
+    for k, fr in enumerate(frames[:6]):
+        app_ref, ll_ref = oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax,
+                                        fr.rx, priors=fr.priors_or_uniform(), kappa=2.0)
+        check_app(apps[k], app_ref, what=f"frame {k}")
+        check_ll(ll[k], ll_ref, what=f"frame {k}")
+
+
+def test_tuner_end_to_end(tmp_path):
+    mapdec.mapdec_tune_clear()
+    frames = _frames(16, 900)
+    st0, app0, ll0 = _decode(frames)
+    table = tune.tune(frames, sample=6, chain_sample=16, reps=1, p_candidates=(0, 4),
+                      nsub_candidates=(0, 2), chain_candidates=((0, 0), (72, 2)))
+    assert table["recursions"]["chain_budget_kb"] in (0, 72)
+    assert {tuple(e[k] for k in ("q", "n", "I")) for e in table["entries"]} == set(tune.classes(frames))
+    path = tmp_path / "table.json"
+    tune.save(table, str(path))
+    mapdec.mapdec_tune_clear()
+    tune.load(str(path))
+    st1, app1, ll1 = _decode(frames)
+    mapdec.mapdec_tune_clear()
+    assert st0 == 0 and st1 == 0
+    for k in range(len(frames)):
+        assert np.abs(app1[k] - app0[k]).max() <= 1e-5, k
+        assert abs(ll1[k] - ll0[k]) <= 1e-9 * abs(ll0[k]), k
