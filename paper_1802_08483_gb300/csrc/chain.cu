@@ -211,8 +211,10 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
     if (threadIdx.x == 0)
         while (issued < NST && issued < total) issue_next();
 
-    // controller state (thread 0); log Z in FP64
-    double logZ = 0.0;
+    // controller state (thread 0); log2 Z as an integer sum of the row
+    // scalings plus the FP64 sum of the tilt terms (changed rows only)
+    long long zexp = 0;
+    double ztilt = 0.0;
     float theta = 1.f;                                    // tilt of the current row
     float mean = (dir == 0) ? 0.f : (float)(send - xmax);  // its mean drift
     float lrow = 0.f;      // log2 of the current row's sum
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
         if (threadIdx.x == 0) {
             theta = (float)cs.theta;
             mean = (float)cs.mean;
-            logZ = cs.logZ;
+            ztilt = cs.logZ / 0.6931471805599453;
             lc_prev = (float)cs.lc_sum;
             lrow = (float)cs.lrow;
             lc_cnt = cs.lc_cnt;
@@ -396,9 +398,9 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
             if (threadIdx.x == 0) {
                 const float lc = log2f(c);
                 if (dir == 0 && !replay) {
-                    logZ += ((double)(ex - 1) +
-                             (double)(th_new - th_cur) * ((double)n * i + (double)mc)) *
-                            0.6931471805599453;
+                    zexp += ex - 1;
+                    if (th_new != th_cur)
+                        ztilt += (double)(th_new - th_cur) * ((double)n * i + (double)mc);
                     f.thf[i + 1] = (double)th_new;
                     f.mcf[i + 1] = (double)(cm / c);
                 } else if (dir == 1) {
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
             ChainState &cs = f.cst[dir];
             cs.theta = theta;
             cs.mean = mean;
-            cs.logZ = logZ;
+            cs.logZ = ((double)zexp + ztilt) * 0.6931471805599453;
             cs.lc_sum = lc_prev;
             cs.lrow = lrow;
             cs.lc_cnt = lc_cnt;
@@ -454,7 +456,8 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
         if (!(aN > 0.f)) {
             atomicMax(f.status, ST_ZERO);
         } else {
-            *f.loglik = log((double)aN) + logZ - (double)theta * (double)rho * 0.6931471805599453;
+            *f.loglik = log((double)aN) +
+                        ((double)zexp + ztilt - (double)theta * (double)rho) * 0.6931471805599453;
         }
     }
 }

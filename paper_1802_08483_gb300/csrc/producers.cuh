@@ -234,6 +234,70 @@ __global__ void __launch_bounds__(kThreads, GRAD ? 1 : 2) k_bwd(const FrameDev *
         const int S4 = (S + 3) & ~3;
         const int off = ilo - ilo2;  // row of symbol ilo in the accumulators
 
+        // (B) alpha and beta windows of the sub-tile's symbols, with the exact
+        // factor that undoes the chains' tilts (k_chain):
+        //   sigma ~ alpha^_i(m') beta^_{i+1}(m) 2^{(theta'_{i+1} - theta_i)(m' - mean_i)}
+        //           2^{(theta'_{i+1} - 1) j} prior R~
+        // up to a constant per symbol.  The per-j factor 2^{phi j}, phi =
+        // theta'_{i+1} - 1, splits exactly as 2^{phi (pl + j)} 2^{-phi pl}: folded
+        // into the beta window (index pl + j) and the alpha window (index pl).
+        // With m' = p0 + pl - n i the alpha-side exponent is e0_i + g_i pl,
+        // e0_i = (theta'_{i+1} - theta_i)(p0 - n i - mean_i) (FP64, split into
+        // integer and fraction), g_i = theta'_{i+1} - theta_i - phi; the factor
+        // is applied as alpha 2^frac scaled by 2^int (exact), clamped below
+        // overflow.  The tilts and means are FP32 values, so e0_i is formed
+        // exactly enough in FP32 pairs (error-free sum and product): its integer
+        // part exactly, its fraction to a few FP32 ulps.  The raw rows are
+        // fetched here, row by row (coalesced), by asynchronous copies that
+        // land while the lattices below run.
+        for (int il = threadIdx.x; il < S4; il += blockDim.x) {
+            int ei = 0;
+            float ef = 0.f, g = 0.f, phi = 0.f;
+            if (il < S) {
+                const long long i = ilo + il;
+                const float tb = (float)f.thb[i + 1], tf = (float)f.thf[i];
+                const float mu = (float)f.mcf[i];
+                // dth = tb - tf and x = (p0 - n i) - mu as unevaluated sums hi + lo
+                float dh, dl, xh, xl;
+                two_sum(tb, -tf, dh, dl);
+                two_sum((float)(p0 - (long long)n * i), -mu, xh, xl);
+                // e0 = dth x = ph + pl + (dh xl + dl xh) (dl xl is far below FP32 ulp)
+                const float ph0 = dh * xh;
+                const float pl0 = fmaf(dh, xh, -ph0);
+                const float r = rintf(ph0);
+                ei = (int)fmaxf(-100000.f, fminf(100000.f, r));
+                ef = ((ph0 - r) + pl0) + fmaf(dh, xl, dl * xh);
+                phi = tb - 1.f;
+                g = (dh - phi) + dl;
+            }
+            symE[il] = ei;
+            symF[il] = ef;
+            symG[il] = g;
+            symPhi[il] = phi;
+        }
+        {
+            // one symbol per warp, positions across the lanes (no divisions)
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
+            for (int il = warp; il < S4; il += NW) {
+                const long long i = ilo + il;
+                const long long sa = p0 - (long long)n * i + xmax;  // state of position p0
+                const float *arow = f.alpha + (size_t)i * f.Mp;
+                const float *brow = f.beta + (size_t)(i + 1) * f.Mp;
+                for (int pl = lane; pl < P; pl += 32) {
+                    const long long s = sa + pl;
+                    float *dst = Aw + pl * S4 + il;
+                    if (il < S && s >= 0 && s < M && p0 + pl <= rho) cp_async4(dst, arow + s);
+                    else *dst = 0.f;
+                }
+                for (int k = lane; k < BW; k += 32) {
+                    const long long s = sa - n + k;
+                    float *dst = Bw + k * S4 + il;
+                    if (il < S && s >= 0 && s < M) cp_async4(dst, brow + s);
+                    else *dst = 0.f;
+                }
+            }
+        }
+
         // (A) receiver metrics (and tangents); lanes cover consecutive D for one p.
         // Decode mode with stored metrics: copy the tile's block instead.
         if (!GRAD && f.Rg) {
@@ -267,65 +331,35 @@ __global__ void __launch_bounds__(kThreads, GRAD ? 1 : 2) k_bwd(const FrameDev *
                 Rt[(size_t)row * CW + th * DS + col] = 0.f;
             }
         }
-        // (B) alpha and beta windows of the sub-tile's symbols, with the exact
-        // factor that undoes the chains' tilts (k_chain):
-        //   sigma ~ alpha^_i(m') beta^_{i+1}(m) 2^{(theta'_{i+1} - theta_i)(m' - mean_i)}
-        //           2^{(theta'_{i+1} - 1) j} prior R~
-        // up to a constant per symbol.  The per-j factor 2^{phi j}, phi =
-        // theta'_{i+1} - 1, splits exactly as 2^{phi (pl + j)} 2^{-phi pl}: folded
-        // into the beta window (index pl + j) and the alpha window (index pl).
-        // With m' = p0 + pl - n i the alpha-side exponent is e0_i + g_i pl,
-        // e0_i = (theta'_{i+1} - theta_i)(p0 - n i - mean_i) (FP64, split into
-        // integer and fraction), g_i = theta'_{i+1} - theta_i - phi; the factor
-        // is applied as alpha 2^frac scaled by 2^int (exact), clamped below
-        // overflow.
-        for (int il = threadIdx.x; il < S4; il += blockDim.x) {
-            int ei = 0;
-            float ef = 0.f, g = 0.f, phi = 0.f;
-            if (il < S) {
-                const long long i = ilo + il;
-                const double dth = f.thb[i + 1] - f.thf[i];
-                const double ph = f.thb[i + 1] - 1.0;
-                const double e0 = dth * ((double)(p0 - (long long)n * i) - f.mcf[i]);
-                const double r = rint(e0);
-                ei = (int)fmax(-100000.0, fmin(100000.0, r));
-                ef = (float)(e0 - r);
-                g = (float)(dth - ph);
-                phi = (float)ph;
-            }
-            symE[il] = ei;
-            symF[il] = ef;
-            symG[il] = g;
-            symPhi[il] = phi;
-        }
+        // (B) the windows' raw alpha/beta values have landed: apply the tilt
+        // factors in place (see above).
+        cp_async_wait_all();
         __syncthreads();
-        for (int idx = threadIdx.x; idx < P * S4; idx += blockDim.x) {
-            const int pl = idx / S4, il = idx - pl * S4;
-            const long long i = ilo + il, p = p0 + pl;
-            const long long s = p - (long long)n * i + xmax;
-            float v = 0.f;
-            if (il < S && s >= 0 && s < M && p <= rho) {
-                const float a = f.alpha[(size_t)i * f.Mp + s];
-                if (a > 0.f) {
-                    const float e = fmaf(symG[il], (float)pl, symF[il]);
-                    const float k = rintf(e);
-                    const int ex = symE[il] + (int)k;
-                    v = a * exp2f(e - k);
-                    v = fminf(ldexpf(v, min(max(ex, -300), 300)), 3.0e38f);
+        {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
+            for (int il = warp; il < S; il += NW) {
+                const float g = symG[il], fr = symF[il], phi = symPhi[il];
+                const int e0 = symE[il];
+                for (int pl = lane; pl < P; pl += 32) {
+                    float *ap = Aw + pl * S4 + il;
+                    const float a = *ap;
+                    if (a > 0.f) {
+                        const float e = fmaf(g, (float)pl, fr);
+                        const float k = rintf(e);
+                        const int ex = min(max(e0 + (int)k, -300), 300);
+                        // 2^ex as two exact powers of two within the FP32 exponent range
+                        const int e1 = min(max(ex, -126), 127);
+                        const int e2 = min(max(ex - e1, -126), 127);
+                        const float v = a * exp2f(e - k);
+                        *ap = fminf(v * pow2i(e1) * pow2i(e2), 3.0e38f);
+                    }
+                }
+                for (int k = lane; k < BW; k += 32) {
+                    float *bp = Bw + k * S4 + il;
+                    const float b = *bp;
+                    if (b != 0.f) *bp = b * exp2f(phi * (float)k);
                 }
             }
-            Aw[idx] = v;
-        }
-        for (int idx = threadIdx.x; idx < BW * S4; idx += blockDim.x) {
-            const int k = idx / S4, il = idx - k * S4;
-            const long long i = ilo + il;
-            const long long s = p0 - (long long)n * i + xmax - n + k;
-            float v = 0.f;
-            if (il < S && s >= 0 && s < M) {
-                const float b = f.beta[(size_t)(i + 1) * f.Mp + s];
-                v = b * exp2f(symPhi[il] * (float)k);
-            }
-            Bw[idx] = v;
         }
         __syncthreads();
 
