@@ -201,6 +201,110 @@ def host_cores() -> int:
 
 
 # ---------------------------------------------------------------------------
+# per-configuration report (--configs): every synthetic configuration in the
+# launch shape it calls for, device-timed, with algorithmic FP32 rates
+# ---------------------------------------------------------------------------
+def _time_ms(fn, reps=5, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def run_configs(fp32_peak):
+    import torch
+    from paper_1802_08483_gb300 import mapdec
+    out = []
+
+    def report(name, frames, ms, flops, extra=None):
+        bits = sum(f.info_bits for f in frames)
+        line = {"report": name, "frames": len(frames), "ms": round(ms, 4),
+                "bits_per_s": bits / (ms / 1e3), "algorithmic_tflops": flops / (ms / 1e3) / 1e12,
+                "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / fp32_peak}
+        line.update(extra or {})
+        print(json.dumps(line), flush=True)
+        out.append(line)
+
+    def flops_of(frames, grad=False):
+        tot = 0
+        for f in frames:
+            ff = frame_flops(f)
+            tot += ff["forward"] + ff["chains"] + ff["backward"]
+            if grad:
+                tot += 3 * ff["lattice"]  # the three tangent lattices of the APP producer
+        return tot
+
+    def batch_run(frames, flags, grad=False):
+        b = mapdec.Batch(frames, flags=flags)
+        rx, pr = b.concat_inputs()
+        if grad:
+            st = b.loglik_grad(rx, pr)[0]  # stages the inputs in the resident buffers
+            rx_d, pr_d, _, _ = mapdec.mapdec_batch_buffers(b.b)
+            dchan = torch.empty(3 * b.nf, dtype=torch.float64, device="cuda")
+            dpri = torch.empty(b.prior_total, dtype=torch.float32, device="cuda")
+            ll = torch.empty(b.nf, dtype=torch.float64, device="cuda")
+            fn = lambda: mapdec.mapdec_batch_loglik_grad(b.b, rx_d, pr_d, dchan, dpri, ll)  # noqa: E731
+        else:
+            st = b.decode(rx, pr)[0]
+            fn = lambda: mapdec.mapdec_batch_run(b.b)  # noqa: E731
+        if st != 0:
+            raise RuntimeError(mapdec.mapdec_strerror(st))
+        return b, fn
+
+    # config 1 and 2: one frame, plain path (one frame per call, default tiles)
+    for cfg in (1, 2):
+        fr = synth.config_frame(cfg, 0)
+        dec = mapdec.Decoder.for_frame(fr)
+        ms = _time_ms(lambda: dec.decode(fr.rx, fr.priors_or_uniform()))
+        report(f"config {cfg}: one frame, plain decode call (host buffers)", [fr], ms,
+               flops_of([fr]))
+        dec.close()
+    # config 2: receiver metrics stored in HBM versus recomputed (batch of one, graph)
+    fr = synth.config_frame(2, 0)
+    key = (fr.q, fr.n, fr.I)
+    for store in (0, 1):
+        mapdec.mapdec_tune_set(*key, {"store_metric": store})
+        b, fn = batch_run([fr], mapdec.MAPDEC_BATCH_GRAPH)
+        ms = _time_ms(fn)
+        T = (fr.rho + 1)
+        rbytes = 2 * T * ((fr.q + 3) // 4 * 4) * (fr.n * (fr.I + 1) + 1) * 4 if store else 0
+        report(f"config 2: one frame, graph, R {'stored in HBM' if store else 'recomputed'}",
+               [fr], ms, flops_of([fr]) - (frame_flops(fr)["lattice"] if store else 0),
+               {"R_bytes_written_and_read": rbytes,
+                "R_traffic_GBps": rbytes / (ms / 1e3) / 1e9})
+        b.close()
+    mapdec.mapdec_tune_set(*key, None)
+    # config 4: 256 frames, log-likelihood and gradients, alpha checkpoint every 45 symbols
+    os.environ["MAPDEC_SEG_K"] = "45"
+    frames = synth.config_frames(4)
+    b, fn = batch_run(frames, mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_GRAD |
+                      mapdec.MAPDEC_BATCH_SEGMENTED, grad=True)
+    ms = _time_ms(fn, reps=3, warm=1)
+    report("config 4: 256 frames N=2000, log P + gradients, checkpoint every 45 symbols",
+           frames, ms, flops_of(frames, grad=True))
+    b.close()
+    os.environ.pop("MAPDEC_SEG_K", None)
+    # config 5: 64 frames N=8000, q=64, n=12, I=3, checkpointed (K = ceil(sqrt(N)))
+    frames = synth.config_frames(5)
+    b, fn = batch_run(frames, mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_SEGMENTED)
+    ms = _time_ms(fn, reps=3, warm=1)
+    report("config 5: 64 frames N=8000, decode, checkpoint every ceil(sqrt(N)) symbols",
+           frames, ms, flops_of(frames) + sum(frame_flops(f)["lattice"] for f in frames),
+           {"note": "the forward producers run twice (recording and recompute sweeps)"})
+    b.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +317,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=20.0)
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the benchmark line, report every synthetic configuration")
     ap.add_argument("--tuning", default=DEFAULT_TUNING,
                     help="tuning table (JSON written by paper_1802_08483_gb300.tune); '' = none")
     ap.add_argument("--mem-budget-gb", type=float, default=0.0,
@@ -285,6 +391,11 @@ def main():
         from paper_1802_08483_gb300 import tune as libtune
         libtune.load(args.tuning)
         tuning = os.path.relpath(args.tuning, ROOT)
+
+    if args.configs:
+        props = torch.cuda.get_device_properties(local_rank)
+        run_configs(props.multi_processor_count * 128 * 2 * 2070.0e6 / 1e12)
+        return 0
 
     # ---- workload ----
     t0 = time.time()

@@ -233,6 +233,8 @@ int mapdec_batch_status(mapdec_batch_t *b, int *status_per_frame);
  * Decode all frames: copies rx_all / priors_all (host or device; priors_all
  * may be NULL = uniform) into the resident buffers, runs, and copies APPs and
  * log-likelihoods to app_all / loglik_all (host or device, may be NULL).
+ * Passing the batch's own resident buffers (mapdec_batch_buffers) as inputs
+ * skips their copy.
  */
 int mapdec_batch_decode(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
                         float *app_all, double *loglik_all);
@@ -240,6 +242,7 @@ int mapdec_batch_decode(mapdec_batch_t *b, const uint8_t *rx_all, const float *p
 /*
  * Gradients for every frame (batch created with MAPDEC_BATCH_GRAD):
  * dchan_all[3*f + k] = d logP_f / d(Pi, Pd, Ps)_k, dpriors_all like app_all.
+ * Inputs as for mapdec_batch_decode.
  */
 int mapdec_batch_loglik_grad(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
                              double *dchan_all, float *dpriors_all, double *loglik_all);

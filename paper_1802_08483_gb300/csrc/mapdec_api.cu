@@ -53,7 +53,7 @@ bool is_device_ptr(const void *p) {
 }
 
 void copy_in(void *dst_dev, const void *src, size_t bytes, cudaStream_t st) {
-    if (bytes == 0) return;
+    if (bytes == 0 || src == dst_dev) return;  // already resident (caller passed the batch's own buffer)
     CK(cudaMemcpyAsync(dst_dev, src, bytes,
                        is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
 }
