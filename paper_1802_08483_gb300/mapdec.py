@@ -104,11 +104,13 @@ def header_symbols() -> list:
 
 
 def load(path: Optional[str] = None):
-    """Load libmapdec.so (raises if it has not been built)."""
+    """Load libmapdec.so (raises if it has not been built).  The environment
+    variable MAPDEC_LIB names an alternative build of the same library (for
+    comparing kernel variants); by default the in-tree build is loaded."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or os.environ.get("MAPDEC_LIB") or LIB_PATH  # MAPDEC_LIB: an alternative build
     if not os.path.exists(path):
         raise RuntimeError(f"libmapdec.so not found at {path}; run __graft_entry__.build() "
                            "(the decoder has no CPU fallback)")
