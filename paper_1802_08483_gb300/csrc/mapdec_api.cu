@@ -380,6 +380,7 @@ struct mapdec_batch {
     bool timing = false;
     bool segmented = false;
     int chain_threads = 0;  // 0: the chain kernel's default
+
     std::vector<cudaEvent_t> events;  // per wave and phase: begin, end
 
     void *dalloc(size_t bytes) {
@@ -394,6 +395,7 @@ struct mapdec_batch {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (aux_stream) cudaStreamDestroy(aux_stream);
         for (cudaEvent_t e : dep) cudaEventDestroy(e);
+
         for (void *p : allocs) cudaFree(p);
     }
 };
@@ -726,7 +728,8 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
 }
 
 // Enqueue one full run on stream st (producers) and the batch's auxiliary
-// stream (chains).  Per wave w: pack and forward producers on st; the chains
+// stream (chains).  The received bits of every wave are packed first.  Per
+// wave w: forward producers on st; the chains
 // on the auxiliary stream after the forward producers; the backward producers
 // and finalize on st after the chains.  The forward producers of wave w+1 are
 // issued before the backward producers of wave w, so they overlap wave w's
@@ -744,15 +747,19 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
     };
     cudaEvent_t fork = b->dep[2 * W], join = b->dep[2 * W + 1];
     CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->nframes * 4, st));
+    // received bits of every wave first (a batch-wide buffer): the packing
+    // kernels then never wait behind recursions for a place on the GPU
+    for (int w = 0; w < W; ++w) {
+        Wave &wv = b->waves[w];
+        mark(w, 0, 0, st);
+        CK(launch_pack(wv.d_frames, wv.d_rxptr, wv.d_rxwptr, wv.f1 - wv.f0, wv.max_words, st));
+        ++launches;
+        mark(w, 0, 1, st);
+    }
     CK(cudaEventRecord(fork, st));
     CK(cudaStreamWaitEvent(cs, fork, 0));
     auto forward = [&](int w) {
         Wave &wv = b->waves[w];
-        const int nw = wv.f1 - wv.f0;
-        mark(w, 0, 0, st);
-        CK(launch_pack(wv.d_frames, wv.d_rxptr, wv.d_rxwptr, nw, wv.max_words, st));
-        ++launches;
-        mark(w, 0, 1, st);
         mark(w, 1, 0, st);
         for (auto &c : wv.cls) {
             CK(launch_fwd(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
