@@ -182,6 +182,15 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     f.fin_base = 0;
     f.fin_total = finalize_chunks(d.N);
     f.chain_flags = 0;
+    // bounded waits: a recursion gives up on a copy after this many polls
+    f.wait_limit = 1u << 26;
+    f.test_flags = 0;
+    if (const char *e = std::getenv("MAPDEC_TEST_STALL_CHAIN")) {  // testing: the timeout path
+        if (std::atoi(e) == 1) {
+            f.test_flags |= TEST_SKIP_FIRST_COPY;
+            f.wait_limit = 4096;
+        }
+    }
     f.ckpt = nullptr;
     f.bedge = nullptr;
     f.cst = nullptr;

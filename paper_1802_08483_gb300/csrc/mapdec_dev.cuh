@@ -17,6 +17,9 @@ namespace mdk {
 constexpr int CH_SEGMENTED = 1;   // start/end rows and controller state come from ckpt/bedge/cst
 constexpr int CH_REPLAY = 2;      // forward chain replays the recorded tilts (recompute sweep)
 
+// test_flags
+constexpr int TEST_SKIP_FIRST_COPY = 1;  // a recursion's first copy is never issued
+
 constexpr int kMaxI = 7;        // insertion cap supported by the kernels
 constexpr int kMaxMN = 64;      // n(I+1) + 1 <= 64 (received window fits 64 bits)
 constexpr int kThreads = 256;   // producer block size
@@ -51,6 +54,8 @@ struct FrameDev {
     int T2;       // backward super-tiles: ceil(T / nsub)
     int chainCD;  // destination/source states per chain chunk
     int chainStages;  // chunks in flight (ring of bulk-copy stages), <= 8
+    uint32_t wait_limit;  // polls before a recursion's wait on a copy gives up (ST_TIMEOUT)
+    int test_flags;       // TEST_SKIP_FIRST_COPY: the first copy is never issued (tests the timeout path)
     long long rho;
     long long wblk;  // floats per symbol block of W (M * MNS rounded up to 4)
     // FP32 lattice constants.  Every received bit carries a weight kappa: the

@@ -293,3 +293,45 @@ def test_fp32_fma_peak_probe():
     props = torch.cuda.get_device_properties(0)
     nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
     assert 0.5 * nominal <= v <= 1.05 * nominal, (v, nominal)
+
+
+def test_recursion_wait_timeout_reports_status(monkeypatch):
+    """A recursion whose first copy is never issued (test hook) gives up after
+    its bounded wait and reports MAPDEC_ERR_TIMEOUT; the device stays usable and
+    the next decode is correct."""
+    fr = synth.config_frame(1, 0)
+    monkeypatch.setenv("MAPDEC_TEST_STALL_CHAIN", "1")
+    dec = mapdec.Decoder.for_frame(fr)
+    with pytest.raises(mapdec.MapDecError) as e:
+        dec.decode(fr.rx, fr.priors_or_uniform())
+    assert e.value.status == mapdec.MAPDEC_ERR_TIMEOUT
+    dec.close()
+    b = mapdec.Batch([fr, synth.config_frame(3, 1)], flags=mapdec.MAPDEC_BATCH_GRAPH)
+    rx, pr = b.concat_inputs()
+    st, _, _ = b.decode(rx, pr)
+    assert st == mapdec.MAPDEC_ERR_TIMEOUT
+    b.close()
+    monkeypatch.delenv("MAPDEC_TEST_STALL_CHAIN")
+    dec = mapdec.Decoder.for_frame(fr)
+    app, ll = dec.decode(fr.rx, fr.priors_or_uniform())
+    dec.close()
+    app_ref, ll_ref = oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                                    priors=fr.priors_or_uniform())
+    check_app(app, app_ref)
+    check_ll(ll, ll_ref)
+
+
+def test_nan_priors_rejected_by_the_recursion():
+    """Host-injected fault: NaN priors poison the transition sums; the forward
+    recursion's normaliser check reports MAPDEC_ERR_ZERO_PROB instead of
+    returning NaNs, and the handle decodes valid priors afterwards."""
+    fr = synth.config_frame(1, 0)
+    dec = mapdec.Decoder.for_frame(fr)
+    pri = fr.priors_or_uniform().astype(np.float32).copy()
+    pri[fr.N // 2, :] = np.nan
+    with pytest.raises(mapdec.MapDecError) as e:
+        dec.decode(fr.rx, pri)
+    assert e.value.status == mapdec.MAPDEC_ERR_ZERO_PROB
+    app, ll = dec.decode(fr.rx, fr.priors_or_uniform())
+    assert np.isfinite(ll) and np.all(np.isfinite(app))
+    dec.close()
