@@ -63,8 +63,8 @@ __device__ __forceinline__ void eval_metric(const FrameDev &f, long long p, int 
 //       Pr[q][S4]  (priors of the touched symbols, transposed)
 // ---------------------------------------------------------------------------
 template <int NB, int IB>
-__global__ void __launch_bounds__(kThreads) k_fwd(const FrameDev *__restrict__ frames,
-                                                  const Work *__restrict__ work) {
+__device__ __forceinline__ void fwd_body(const FrameDev *__restrict__ frames,
+                                         const Work *__restrict__ work) {
     const Work wk = work[blockIdx.x];
     const FrameDev &f = frames[wk.frame];
     const int n = (NB == 0) ? f.n : NB;
@@ -172,6 +172,20 @@ __global__ void __launch_bounds__(kThreads) k_fwd(const FrameDev *__restrict__ f
             }
         }
     }
+}
+
+// Two register budgets: the compiler's own (I <= 2 classes fit two CTAs per SM
+// with it) and at most 128 registers (I >= 3, whose longer lattice rows would
+// otherwise hold one CTA per SM).
+template <int NB, int IB>
+__global__ void __launch_bounds__(kThreads) k_fwd(const FrameDev *__restrict__ frames,
+                                                  const Work *__restrict__ work) {
+    fwd_body<NB, IB>(frames, work);
+}
+template <int NB, int IB>
+__global__ void __launch_bounds__(kThreads, 2) k_fwd_occ2(const FrameDev *__restrict__ frames,
+                                                          const Work *__restrict__ work) {
+    fwd_body<NB, IB>(frames, work);
 }
 
 // ---------------------------------------------------------------------------

@@ -10,16 +10,20 @@ constexpr int kMaxDynSmem = 227 * 1024;  // producers use no static shared memor
 
 template <int NB, int IB>
 cudaError_t launch_fwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem, cudaStream_t st) {
+    // I >= 3: the 128-register build (two CTAs per SM)
+    auto kern = [] {
+        if constexpr (IB >= 3) return k_fwd_occ2<NB, IB>;
+        else return k_fwd<NB, IB>;
+    }();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_fwd<NB, IB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kMaxDynSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     if (nw <= 0) return cudaSuccess;
-    k_fwd<NB, IB><<<nw, kThreads, smem, st>>>(fr, w);
+    kern<<<nw, kThreads, smem, st>>>(fr, w);
     return cudaGetLastError();
 }
 
