@@ -220,7 +220,7 @@ def _time_ms(fn, reps=5, warm=2):
     return best
 
 
-def run_configs(fp32_peak):
+def run_configs(fp32_peak, which=(1, 2, 4, 5)):
     import torch
     from paper_1802_08483_gb300 import mapdec
     out = []
@@ -240,7 +240,8 @@ def run_configs(fp32_peak):
             ff = frame_flops(f)
             tot += ff["forward"] + ff["chains"] + ff["backward"]
             if grad:
-                tot += 3 * ff["lattice"]  # the three tangent lattices of the APP producer
+                # the three tangent lattices and their contractions in the APP producer
+                tot += 3 * ff["lattice"] + 3 * 2 * f.q * ff["V"]
         return tot
 
     def batch_run(frames, flags, grad=False):
@@ -261,7 +262,7 @@ def run_configs(fp32_peak):
         return b, fn
 
     # config 1 and 2: one frame, plain path (one frame per call, default tiles)
-    for cfg in (1, 2):
+    for cfg in [c for c in (1, 2) if c in which]:
         fr = synth.config_frame(cfg, 0)
         dec = mapdec.Decoder.for_frame(fr)
         ms = _time_ms(lambda: dec.decode(fr.rx, fr.priors_or_uniform()))
@@ -270,8 +271,10 @@ def run_configs(fp32_peak):
         dec.close()
     # config 2: receiver metrics stored in HBM versus recomputed (batch of one, graph)
     fr = synth.config_frame(2, 0)
-    key = (fr.q, fr.n, fr.I)
-    for store in (0, 1):
+    if 2 not in which:
+        fr = None
+    key = (fr.q, fr.n, fr.I) if fr is not None else None
+    for store in ((0, 1) if fr is not None else ()):
         mapdec.mapdec_tune_set(*key, {"store_metric": store})
         b, fn = batch_run([fr], mapdec.MAPDEC_BATCH_GRAPH)
         ms = _time_ms(fn)
@@ -282,8 +285,13 @@ def run_configs(fp32_peak):
                {"R_bytes_written_and_read": rbytes,
                 "R_traffic_GBps": rbytes / (ms / 1e3) / 1e9})
         b.close()
-    mapdec.mapdec_tune_set(*key, None)
+    if key is not None:
+        mapdec.mapdec_tune_set(*key, None)
+    if 4 not in which and 5 not in which:
+        return out
     # config 4: 256 frames, log-likelihood and gradients, alpha checkpoint every 45 symbols
+    if 4 not in which:
+        return _config5(out, report, flops_of, batch_run) if 5 in which else out
     os.environ["MAPDEC_SEG_K"] = "45"
     frames = synth.config_frames(4)
     b, fn = batch_run(frames, mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_GRAD |
@@ -293,6 +301,11 @@ def run_configs(fp32_peak):
            frames, ms, flops_of(frames, grad=True))
     b.close()
     os.environ.pop("MAPDEC_SEG_K", None)
+    return _config5(out, report, flops_of, batch_run) if 5 in which else out
+
+
+def _config5(out, report, flops_of, batch_run):
+    from paper_1802_08483_gb300 import mapdec
     # config 5: 64 frames N=8000, q=64, n=12, I=3, checkpointed (K = ceil(sqrt(N)))
     frames = synth.config_frames(5)
     b, fn = batch_run(frames, mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_SEGMENTED)
@@ -317,8 +330,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=20.0)
-    ap.add_argument("--configs", action="store_true",
-                    help="instead of the benchmark line, report every synthetic configuration")
+    ap.add_argument("--configs", nargs="?", const="1,2,4,5", default=None,
+                    help="instead of the benchmark line, report synthetic configurations "
+                         "(comma list; default 1,2,4,5)")
     ap.add_argument("--tuning", default=DEFAULT_TUNING,
                     help="tuning table (JSON written by paper_1802_08483_gb300.tune); '' = none")
     ap.add_argument("--mem-budget-gb", type=float, default=0.0,
@@ -394,7 +408,8 @@ def main():
 
     if args.configs:
         props = torch.cuda.get_device_properties(local_rank)
-        run_configs(props.multi_processor_count * 128 * 2 * 2070.0e6 / 1e12)
+        run_configs(props.multi_processor_count * 128 * 2 * 2070.0e6 / 1e12,
+                    {int(c) for c in args.configs.split(",")})
         return 0
 
     # ---- workload ----

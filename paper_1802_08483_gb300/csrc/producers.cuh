@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_occ2(const FrameDev *__rest
 //       symbol constants (3 x S4), Lacc[S2][q], Gacc[S2][3], Ct[3][S4][DS] (gradient)
 // ---------------------------------------------------------------------------
 template <int NB, int IB, bool GRAD>
-__global__ void __launch_bounds__(kThreads, GRAD ? 1 : 2) k_bwd(const FrameDev *__restrict__ frames,
+__global__ void __launch_bounds__(kThreads, (GRAD && (NB == 0 || NB > 10)) ? 1 : 2) k_bwd(const FrameDev *__restrict__ frames,
                                                      const Work *__restrict__ work) {
     constexpr int NR = GRAD ? 4 : 1;
     const Work wk = work[blockIdx.x];
