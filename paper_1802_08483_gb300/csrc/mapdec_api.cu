@@ -304,8 +304,8 @@ size_t frame_scratch_floats_seg(const FrameDev &f, int K, int S, bool grad) {
     const int T2s = seg_supertiles(f, K);
     const int cps = finalize_chunks(K);
     size_t s = 0;
-    s += rup((size_t)K * f.wblk + 16, 64);               // W of one segment
-    s += rup((size_t)(K + 1) * f.Mp, 64) * 2;            // alpha, beta rows of one segment
+    s += 2 * rup((size_t)K * f.wblk + 16, 64);           // W of a segment, two buffers
+    s += 4 * rup((size_t)(K + 1) * f.Mp, 64);            // alpha, beta rows of a segment, two buffers
     s += rup((size_t)T2s * f.S2 * f.q, 64);              // Lp of one segment
     if (grad) s += rup((size_t)T2s * f.S2 * 3, 64);      // Gp
     s += 3 * rup((size_t)(f.N + 1) * 2, 64);             // thf, mcf, thb
@@ -338,6 +338,9 @@ struct SegLaunch {
     Work *d_bw = nullptr; int nbw = 0;      // forward replay + backward chains
     Work *d_fin = nullptr; int nfin = 0;
     int nframes = 0;
+    // order between the producer stream and the recursion stream
+    cudaEvent_t ev_fwd = nullptr, ev_rec = nullptr;             // recording sweep
+    cudaEvent_t ev_fwd2 = nullptr, ev_chain2 = nullptr, ev_bwd = nullptr;  // recompute sweep
 };
 
 struct Wave {
@@ -391,6 +394,7 @@ struct mapdec_batch {
     int chain_threads = 0;  // 0: the chain kernel's default
 
     std::vector<cudaEvent_t> events;  // per wave and phase: begin, end
+    std::vector<cudaEvent_t> seg_events;  // segmented runs: ordering events of every segment
 
     void *dalloc(size_t bytes) {
         void *p = nullptr;
@@ -401,6 +405,7 @@ struct mapdec_batch {
     ~mapdec_batch() {
         if (gexec) cudaGraphExecDestroy(gexec);
         for (cudaEvent_t e : events) cudaEventDestroy(e);
+        for (cudaEvent_t e : seg_events) cudaEventDestroy(e);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (aux_stream) cudaStreamDestroy(aux_stream);
         for (cudaEvent_t e : dep) cudaEventDestroy(e);
@@ -453,9 +458,11 @@ void build_segments(mapdec_batch *b, Wave &w, const std::vector<FrameDev> &devs,
             };
             f.seg_i0 = i0;
             f.seg_i1 = i1;
-            f.W = (float *)shift(devs[k].W, (long long)i0 * f.wblk * 4);
-            f.alpha = (float *)shift(devs[k].alpha, (long long)i0 * f.Mp * 4);
-            f.beta = (float *)shift(devs[k].beta, (long long)i0 * f.Mp * 4);
+            const size_t wst = rup((size_t)K * f.wblk + 16, 64), ast = rup((size_t)(K + 1) * f.Mp, 64);
+            const size_t buf = (size_t)(s & 1);
+            f.W = (float *)shift(devs[k].W + buf * wst, (long long)i0 * f.wblk * 4);
+            f.alpha = (float *)shift(devs[k].alpha + buf * ast, (long long)i0 * f.Mp * 4);
+            f.beta = (float *)shift(devs[k].beta + buf * ast, (long long)i0 * f.Mp * 4);
             f.Lp = (float *)shift(devs[k].Lp, t2first * f.S2 * f.q * 4);
             if (devs[k].Gp) f.Gp = (float *)shift(devs[k].Gp, t2first * f.S2 * 3 * 4);
             f.ckpt = devs[k].ckpt + (size_t)s * f.Mp;
@@ -475,6 +482,10 @@ void build_segments(mapdec_batch *b, Wave &w, const std::vector<FrameDev> &devs,
             if (!v.empty())
                 CK(cudaMemcpy(dst, v.data(), sizeof(Work) * v.size(), cudaMemcpyHostToDevice));
         };
+        for (cudaEvent_t *e : {&sl.ev_fwd, &sl.ev_rec, &sl.ev_fwd2, &sl.ev_chain2, &sl.ev_bwd}) {
+            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+            b->seg_events.push_back(*e);
+        }
         upload(rec, sl.d_rec, sl.nrec);
         upload(bw, sl.d_bw, sl.nbw);
         upload(fin, sl.d_fin, sl.nfin);
@@ -638,9 +649,11 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
                 // buffers of one segment; per-segment descriptors shift their bases
                 const int K = h.segK, S = h.nseg;
                 const int T2s = seg_supertiles(f, K), cps = finalize_chunks(K);
-                f.W = base + o; o += rup((size_t)K * f.wblk + 16, 64);
-                f.alpha = base + o; o += rup((size_t)(K + 1) * f.Mp, 64);
-                f.beta = base + o; o += rup((size_t)(K + 1) * f.Mp, 64);
+                // W, alpha and beta twice: segment s uses buffer s % 2, so a
+                // segment's producers overlap the neighbouring segment's recursions
+                f.W = base + o; o += 2 * rup((size_t)K * f.wblk + 16, 64);
+                f.alpha = base + o; o += 2 * rup((size_t)(K + 1) * f.Mp, 64);
+                f.beta = base + o; o += 2 * rup((size_t)(K + 1) * f.Mp, 64);
                 f.Lp = base + o; o += rup((size_t)T2s * f.S2 * f.q, 64);
                 f.Gp = nullptr;
                 if (b->grad) { f.Gp = base + o; o += rup((size_t)T2s * f.S2 * 3, 64); }
@@ -809,56 +822,82 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
     return launches;
 }
 
-// Segmented run (checkpoint and recompute), all on stream st.  Per wave: pack;
-// a recording sweep over the segments in order (forward producers of the
-// segment, then the forward chains, which write the tilts and a checkpoint row
-// at every segment boundary); then a sweep over the segments in reverse, each
-// recomputing its W, replaying the forward chain from its checkpoint with the
-// recorded tilts (bit-identical rows) next to the backward chain, then the APP
-// producers and finalize of the segment.  The gradient chunks are added up
-// after the last (first) segment.  Timing phases: pack, recording sweep
-// (forward), backward sweep (backward); chains and finalize read 0.
+// Segmented run (checkpoint and recompute) on the producer stream st and the
+// recursion stream.  Per wave: pack; a recording sweep over the segments in
+// order (forward producers of the segment, then the forward recursions, which
+// write the tilts and a checkpoint row at every segment boundary); then a sweep
+// over the segments in reverse, each recomputing its W, replaying the forward
+// recursion from its checkpoint with the recorded tilts (bit-identical rows)
+// next to the backward recursion, then the APP producers and finalize of the
+// segment.  W, alpha and beta are double-buffered by segment parity, so the
+// producers of segment s+1 (s-1 in the second sweep) run while the
+// recursions of segment s do; events keep every buffer's readers and writers
+// in order.  The gradient chunks are added up after the last (first) segment.
+// Timing phases: pack, recording-sweep producers (forward), all recursions
+// (chains), recompute-sweep producers and finalize (backward); finalize reads 0.
 int64_t enqueue_run_seg(mapdec_batch *b, bool grad, cudaStream_t st) {
     int64_t launches = 0;
     const int W = (int)b->waves.size();
-    auto mark = [&](int w, int ph, int end) {
+    cudaStream_t cs = b->aux_stream;
+    auto mark = [&](int w, int ph, int end, cudaStream_t s) {
         if (b->timing)
-            CK(cudaEventRecordWithFlags(b->events[((size_t)w * kPhases + ph) * 2 + end], st,
+            CK(cudaEventRecordWithFlags(b->events[((size_t)w * kPhases + ph) * 2 + end], s,
                                         cudaEventRecordExternal));
     };
+    cudaEvent_t fork = b->dep[2 * W], join = b->dep[2 * W + 1];
     CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->nframes * 4, st));
     for (int w = 0; w < W; ++w) {
         Wave &wv = b->waves[w];
         const int nw = wv.f1 - wv.f0;
         const int S = (int)wv.segs.size();
-        mark(w, 0, 0);
+        mark(w, 0, 0, st);
         CK(launch_pack(wv.d_frames, wv.d_rxptr, wv.d_rxwptr, nw, wv.max_words, st));
         ++launches;
-        mark(w, 0, 1);
-        mark(w, 1, 0);
+        mark(w, 0, 1, st);
+        CK(cudaEventRecord(fork, st));
+        CK(cudaStreamWaitEvent(cs, fork, 0));
+        mark(w, 1, 0, st);
+        mark(w, 2, 0, cs);
+        auto fwd = [&](SegLaunch &sl) {
+            for (auto &c : sl.cls) {
+                if (c.nfwd == 0) continue;
+                CK(launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
+                ++launches;
+            }
+        };
+        // recording sweep: fwd(s) on st once recording chain s-2 has read its buffer
         for (int s = 0; s < S; ++s) {
             SegLaunch &sl = wv.segs[s];
-            for (auto &c : sl.cls) {
-                if (c.nfwd == 0) continue;
-                CK(launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
-                ++launches;
-            }
-            CK(launch_chain(sl.d_frames, sl.d_rec, sl.nrec, wv.smem_chain, b->chain_threads, st));
+            if (s >= 2) CK(cudaStreamWaitEvent(st, wv.segs[s - 2].ev_rec, 0));
+            fwd(sl);
+            CK(cudaEventRecord(sl.ev_fwd, st));
+            CK(cudaStreamWaitEvent(cs, sl.ev_fwd, 0));
+            CK(launch_chain(sl.d_frames, sl.d_rec, sl.nrec, wv.smem_chain, b->chain_threads, cs));
             ++launches;
+            CK(cudaEventRecord(sl.ev_rec, cs));
         }
-        mark(w, 1, 1);
-        mark(w, 2, 0);
-        mark(w, 2, 1);
-        mark(w, 3, 0);
+        mark(w, 1, 1, st);
+        // the recompute sweep reuses both buffers: every recording chain done
+        CK(cudaStreamWaitEvent(st, wv.segs[S - 1].ev_rec, 0));
+        mark(w, 3, 0, st);
+        auto fwd2 = [&](int s) {
+            SegLaunch &sl = wv.segs[s];
+            // buffer s % 2 was last read by recompute-sweep chain s+2
+            if (s + 2 < S) CK(cudaStreamWaitEvent(st, wv.segs[s + 2].ev_chain2, 0));
+            fwd(sl);
+            CK(cudaEventRecord(sl.ev_fwd2, st));
+            CK(cudaStreamWaitEvent(cs, sl.ev_fwd2, 0));
+            // alpha/beta buffer s % 2 was last read by the APP producers of segment s+2
+            if (s + 2 < S) CK(cudaStreamWaitEvent(cs, wv.segs[s + 2].ev_bwd, 0));
+            CK(launch_chain(sl.d_frames, sl.d_bw, sl.nbw, wv.smem_chain, b->chain_threads, cs));
+            ++launches;
+            CK(cudaEventRecord(sl.ev_chain2, cs));
+        };
+        fwd2(S - 1);
         for (int s = S - 1; s >= 0; --s) {
             SegLaunch &sl = wv.segs[s];
-            for (auto &c : sl.cls) {
-                if (c.nfwd == 0) continue;
-                CK(launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
-                ++launches;
-            }
-            CK(launch_chain(sl.d_frames, sl.d_bw, sl.nbw, wv.smem_chain, b->chain_threads, st));
-            ++launches;
+            if (s >= 1) fwd2(s - 1);  // overlaps the recursions of segment s
+            CK(cudaStreamWaitEvent(st, sl.ev_chain2, 0));
             for (auto &c : sl.cls) {
                 if (c.nbwd == 0) continue;
                 CK(launch_bwd(c.n, c.I, grad, sl.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
@@ -867,10 +906,14 @@ int64_t enqueue_run_seg(mapdec_batch *b, bool grad, cudaStream_t st) {
             CK(launch_finalize(sl.d_frames, sl.d_fin, sl.nfin, nw, grad ? 1 : 0, st,
                                grad && s == 0));
             launches += (grad && s == 0) ? 2 : 1;
+            CK(cudaEventRecord(sl.ev_bwd, st));
         }
-        mark(w, 3, 1);
-        mark(w, 4, 0);
-        mark(w, 4, 1);
+        mark(w, 2, 1, cs);
+        CK(cudaEventRecord(join, cs));
+        CK(cudaStreamWaitEvent(st, join, 0));
+        mark(w, 3, 1, st);
+        mark(w, 4, 0, st);
+        mark(w, 4, 1, st);
     }
     return launches;
 }
