@@ -9,6 +9,11 @@ step by step); this module compiles it with gcc and marshals numpy arrays.
 Every function here is pinned by the ``-m "not gpu"`` tests against brute-force
 enumeration of channel events, closed forms and invariants (see
 ``tests/test_oracle_*.py``).  No function is left "parity unpinned".
+
+``decode_ext`` and ``loglik_grad`` also take per-symbol codebooks (the
+constituent encodings C_i of Sec. II-A) and ``decode_ext`` returns the
+extrinsic outputs used in iterative decoding; the CUDA decoder implements
+neither yet, so these serve as the reference for that next step.
 """
 from __future__ import annotations
 
@@ -76,6 +81,11 @@ def _load():
         lib.orc_forward_backward.restype = ctypes.c_int
         lib.orc_loglik_grad.argtypes = common + [ctypes.c_int, dp, dp, dp]
         lib.orc_loglik_grad.restype = ctypes.c_int
+        general = common[:3] + [ctypes.c_int] + common[3:]
+        lib.orc_decode_general.argtypes = general + [ctypes.c_int, dp, dp, dp]
+        lib.orc_decode_general.restype = ctypes.c_int
+        lib.orc_loglik_grad_general.argtypes = general + [ctypes.c_int, dp, dp, dp]
+        lib.orc_loglik_grad_general.restype = ctypes.c_int
         lib.orc_set_received_bit_weight.argtypes = [ctypes.c_double]
         lib.orc_set_received_bit_weight.restype = None
         _lib = lib
@@ -112,6 +122,8 @@ def receiver_metric(x, y, I: int, Pi: float, Pd: float, Ps: float) -> np.ndarray
 
 def _frame_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors):
     cb, cbp = _u8(codebook)
+    if cb.ndim == 3:
+        raise ValueError("per-symbol codebooks go through decode_ext / loglik_grad")
     q, n = cb.shape
     rxa = np.ascontiguousarray(rx, dtype=np.uint8)
     rbuf = rxa if rxa.size else np.zeros(1, np.uint8)
@@ -172,20 +184,61 @@ def forward_backward(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None):
     return A, B, lc
 
 
-def loglik_grad(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True,
-                want_chan=True, want_priors=True, kappa=1.0):
-    """(logP, d logP/d(Pi,Pd,Ps) or None, d logP/d priors (N,q) or None)."""
+def _general_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors):
+    """Arguments of the general entry points: codebook (q, n) is one codebook
+    for every symbol, (N, q, n) the per-symbol codebooks C_0..C_{N-1}."""
+    cb = np.ascontiguousarray(codebook, dtype=np.uint8)
+    if cb.ndim == 3:
+        if cb.shape[0] != N:
+            raise ValueError(f"per-symbol codebooks: {cb.shape[0]} codebooks for N = {N}")
+        per_symbol = 1
+        flat = cb[0]
+    elif cb.ndim == 2:
+        per_symbol = 0
+        flat = cb
+    else:
+        raise ValueError("codebook must be (q, n) or (N, q, n)")
+    q, n, args, keep = _frame_args(flat, N, Pi, Pd, Ps, I, xmax, rx, priors)
+    args[2] = cb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    keep.append(cb)
+    return q, n, args[:3] + [per_symbol] + args[3:], keep
+
+
+def decode_ext(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True, kappa=1.0):
+    """(APPs (N, q), extrinsic outputs (N, q), log P(Y)) of one frame (FP64).
+
+    codebook is (q, n), one codebook for every symbol, or (N, q, n), the
+    constituent encodings C_i of Sec. II-A.  The extrinsic output of symbol i
+    is eq. (L) without the symbol's own prior, normalised over D."""
     lib = _load()
     lib.orc_set_received_bit_weight(float(kappa))
-    q, n, args, keep = _frame_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
+    q, n, args, keep = _general_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
+    dpp = ctypes.POINTER(ctypes.c_double)
+    app = np.zeros((N, q), np.float64)
+    ext = np.zeros((N, q), np.float64)
+    ll = ctypes.c_double(0.0)
+    st = lib.orc_decode_general(*args, int(bool(memo)), app.ctypes.data_as(dpp),
+                                ext.ctypes.data_as(dpp), ctypes.byref(ll))
+    if st:
+        raise OracleError(st, "decode_ext")
+    return app, ext, ll.value
+
+
+def loglik_grad(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True,
+                want_chan=True, want_priors=True, kappa=1.0):
+    """(logP, d logP/d(Pi,Pd,Ps) or None, d logP/d priors (N,q) or None).
+    codebook is (q, n) or per-symbol (N, q, n), as for decode_ext."""
+    lib = _load()
+    lib.orc_set_received_bit_weight(float(kappa))
+    q, n, args, keep = _general_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
     dpp = ctypes.POINTER(ctypes.c_double)
     dchan = np.zeros(3, np.float64) if want_chan else None
     dpri = np.zeros((N, q), np.float64) if want_priors else None
     ll = ctypes.c_double(0.0)
-    st = lib.orc_loglik_grad(*args, int(bool(memo)),
-                             dchan.ctypes.data_as(dpp) if want_chan else _NULL_D,
-                             dpri.ctypes.data_as(dpp) if want_priors else _NULL_D,
-                             ctypes.byref(ll))
+    st = lib.orc_loglik_grad_general(*args, int(bool(memo)),
+                                     dchan.ctypes.data_as(dpp) if want_chan else _NULL_D,
+                                     dpri.ctypes.data_as(dpp) if want_priors else _NULL_D,
+                                     ctypes.byref(ll))
     if st:
         raise OracleError(st, "loglik_grad")
     return ll.value, dchan, dpri

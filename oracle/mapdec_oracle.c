@@ -10,12 +10,16 @@
  * notation, in double precision:
  *   - receiver metric R(y|x): the lattice of eqs. (F), (F_lastrow) with its
  *     initial conditions, plus a cap of I insertions per transmitted bit;
- *   - gamma_i(m', m, D) = Pr{D_i = D} R(Y[n i + m' .. n(i+1) + m) | C(D)),
- *     eq. (gamma), evaluated on the paper's own (i, m', D) grid;
+ *   - gamma_i(m', m, D) = Pr{D_i = D} R(Y[n i + m' .. n(i+1) + m) | C_i(D)),
+ *     eq. (gamma), evaluated on the paper's own (i, m', D) grid, with one
+ *     codebook for every symbol or a codebook C_i per symbol (the constituent
+ *     encodings of Sec. II-A);
  *   - the forward recursion with per-index normalisation, eqs. (alpha),
  *     (alpha_norm), (alpha_prenorm); the backward recursion eq. (beta),
  *     normalised the same way;
- *   - the APPs, eqs. (L), (lambda), (sigma), normalised over D per symbol;
+ *   - the APPs, eqs. (L), (lambda), (sigma), normalised over D per symbol,
+ *     and the extrinsic outputs (the same sums without the symbol's own
+ *     prior), which an outer decoder takes in iterative decoding (Sec. II-A);
  *   - the frame log-likelihood  log P(Y) = sum_i log c_i + log alpha_N(rho-tau)
  *     where c_i are the forward normalisers of eq. (alpha_norm).
  *
@@ -39,7 +43,9 @@
  *
  * The optional memo caches R(.|C(D)) per (rx start p, D): the same lattice
  * function evaluated once per key, so results are bitwise identical to the
- * un-memoised (i, m', D) grid; it only saves time on large frames.
+ * un-memoised (i, m', D) grid; it only saves time on large frames.  With
+ * per-symbol codebooks the lattice at (p, D) also depends on i, and the memo
+ * is off.
  *
  * Optional received-bit weight kappa (default 1: the literal recursion).  The
  * normalised forward row alpha_i(m) is the probability of a received prefix of
@@ -208,7 +214,8 @@ typedef struct {
     int q, n, N, I, xmax, M, Mn;
     int64_t rho;
     double Pi, Pd, Ps;
-    const uint8_t *cb;  /* q*n codeword bits */
+    const uint8_t *cb;  /* q*n codeword bits, or N*q*n with per-symbol codebooks */
+    size_t cb_stride;   /* 0: C_i = C for every i; q*n: codebook C_i at cb + i*q*n */
     const uint8_t *rx;  /* rho received bits */
     const double *pri;  /* N*q priors, or NULL for uniform 1/q */
     int memo;
@@ -223,8 +230,15 @@ static double orc_prior(const orc_ctx *c, int i, int D)
     return c->pri ? c->pri[(size_t)i * c->q + D] : 1.0 / (double)c->q;
 }
 
-/* R(Y[p .. p+j) | C(D)) for j = 0..Mn-1 (entries with p + j > rho are 0). */
-static int orc_R(orc_ctx *c, int64_t p, int D, double *Rj)
+/* Codeword C_i(D) of the constituent encoding of symbol i (Sec. II-A). */
+static const uint8_t *orc_codeword(const orc_ctx *c, int i, int D)
+{
+    return c->cb + (size_t)i * c->cb_stride + (size_t)D * c->n;
+}
+
+/* R(Y[p .. p+j) | C_i(D)) for j = 0..Mn-1 (entries with p + j > rho are 0).
+   The memo (keyed by p, D) is only used with one codebook for all symbols. */
+static int orc_R(orc_ctx *c, int i, int64_t p, int D, double *Rj)
 {
     const int Mn = c->Mn;
     if (c->memo && c->Rk[p]) {
@@ -234,7 +248,7 @@ static int orc_R(orc_ctx *c, int64_t p, int D, double *Rj)
     int64_t avail = c->rho - p;
     int mu = (int)(avail < (int64_t)(Mn - 1) ? avail : (int64_t)(Mn - 1));
     for (int j = 0; j < Mn; ++j) Rj[j] = 0.0;
-    int st = orc_receiver_metric(c->n, c->I, c->cb + (size_t)D * c->n, c->rx + p, mu,
+    int st = orc_receiver_metric(c->n, c->I, orc_codeword(c, i, D), c->rx + p, mu,
                                  c->Pi, c->Pd, c->Ps, Rj);
     if (st) return st;
     if (c->memo) {
@@ -244,7 +258,7 @@ static int orc_R(orc_ctx *c, int64_t p, int D, double *Rj)
     return ORC_OK;
 }
 
-static int orc_R_dual(orc_ctx *c, int64_t p, int D, dual *Rj)
+static int orc_R_dual(orc_ctx *c, int i, int64_t p, int D, dual *Rj)
 {
     const int Mn = c->Mn;
     if (c->memo && c->Rdk[p]) {
@@ -254,7 +268,7 @@ static int orc_R_dual(orc_ctx *c, int64_t p, int D, dual *Rj)
     int64_t avail = c->rho - p;
     int mu = (int)(avail < (int64_t)(Mn - 1) ? avail : (int64_t)(Mn - 1));
     for (int j = 0; j < Mn; ++j) Rj[j] = d_const(0.0);
-    int st = orc_receiver_metric_dual(c->n, c->I, c->cb + (size_t)D * c->n, c->rx + p, mu,
+    int st = orc_receiver_metric_dual(c->n, c->I, orc_codeword(c, i, D), c->rx + p, mu,
                                       c->Pi, c->Pd, c->Ps, Rj);
     if (st) return st;
     if (c->memo) {
@@ -286,7 +300,7 @@ static int orc_gamma(orc_ctx *c, int i, double *g, double *R)
                 for (int k = 0; k < Mn; ++k) { gd[k] = 0.0; if (Rd) Rd[k] = 0.0; }
                 continue;
             }
-            int st = orc_R(c, p, D, Rj);
+            int st = orc_R(c, i, p, D, Rj);
             if (st) { free(Rj); return st; }
             const double pr = orc_prior(c, i, D);
             double kw = 1.0;  /* kappa^k, k = received length */
@@ -317,7 +331,7 @@ static int orc_gamma_dual(orc_ctx *c, int i, dual *g)
                 for (int k = 0; k < Mn; ++k) gd[k] = d_const(0.0);
                 continue;
             }
-            int st = orc_R_dual(c, p, D, Rj);
+            int st = orc_R_dual(c, i, p, D, Rj);
             if (st) { free(Rj); return st; }
             const double pr = orc_prior(c, i, D);
             double kw = 1.0;
@@ -332,9 +346,9 @@ static int orc_gamma_dual(orc_ctx *c, int i, dual *g)
     return ORC_OK;
 }
 
-static int orc_init(orc_ctx *c, int q, int n, const uint8_t *codebook, int N, double Pi,
-                    double Pd, double Ps, int I, int xmax, const uint8_t *rx, int64_t rho,
-                    const double *priors, int memo, int want_dual)
+static int orc_init(orc_ctx *c, int q, int n, const uint8_t *codebook, int per_symbol, int N,
+                    double Pi, double Pd, double Ps, int I, int xmax, const uint8_t *rx,
+                    int64_t rho, const double *priors, int memo, int want_dual)
 {
     memset(c, 0, sizeof(*c));
     if (q < 2 || n < 1 || n > 62 || N < 1 || I < 1 || xmax < 0 || !codebook || rho < 0 ||
@@ -347,7 +361,11 @@ static int orc_init(orc_ctx *c, int q, int n, const uint8_t *codebook, int N, do
     c->q = q; c->n = n; c->N = N; c->I = I; c->xmax = xmax;
     c->M = 2 * xmax + 1; c->Mn = n * (I + 1) + 1;
     c->rho = rho; c->Pi = Pi; c->Pd = Pd; c->Ps = Ps;
-    c->cb = codebook; c->rx = rx; c->pri = priors; c->memo = memo;
+    c->cb = codebook; c->rx = rx; c->pri = priors;
+    c->cb_stride = per_symbol ? (size_t)q * n : 0;
+    /* with per-symbol codebooks the lattice at (p, D) depends on i as well */
+    c->memo = per_symbol ? 0 : memo;
+    memo = c->memo;
     if (memo) {
         size_t cells = (size_t)(rho + 1) * q * c->Mn;
         if (want_dual) {
@@ -497,15 +515,28 @@ static int orc_app(orc_ctx *c, const double *A, const double *B, double *app, do
 /* ------------------------------------------------------------------ */
 
 /*
- * Full decode of one frame: APPs (N*q, row i sums to 1) and log P(Y).
+ * Full decode of one frame under the constituent encodings of Sec. II-A.
+ * codebooks: per_symbol = 0, one codebook C (q*n bits) used for every symbol;
+ * per_symbol = 1, the codebooks C_0..C_{N-1} (N*q*n bits, C_i at i*q*n).
+ * Outputs, each optional (NULL):
+ *   app    N*q APPs of eq. (L), row i normalised over D;
+ *   ext    N*q extrinsic outputs: E_i(D) proportional to
+ *          sum_{m', m} alpha_i(m') R(Y[n i + m' .. n(i+1) + m) | C_i(D)) beta_{i+1}(m),
+ *          i.e. eq. (L) without the symbol's own prior Pr{D_i = D}, row i
+ *          normalised over D.  This is what the inner decoder hands to an
+ *          outer decoder when the two are decoded iteratively (Sec. II-A, and
+ *          the role of the priors in Sec. II-C);
+ *   loglik log P(Y).
  * priors: N*q, row i = Pr{D_i = .}; NULL means uniform 1/q.
  */
-int orc_decode(int q, int n, const uint8_t *codebook, int N, double Pi, double Pd, double Ps,
-               int I, int xmax, const uint8_t *rx, int64_t rho, const double *priors, int memo,
-               double *app, double *loglik)
+int orc_decode_general(int q, int n, const uint8_t *codebooks, int per_symbol, int N, double Pi,
+                       double Pd, double Ps, int I, int xmax, const uint8_t *rx, int64_t rho,
+                       const double *priors, int memo, double *app, double *ext,
+                       double *loglik)
 {
     orc_ctx c;
-    int st = orc_init(&c, q, n, codebook, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, memo, 0);
+    int st = orc_init(&c, q, n, codebooks, per_symbol, N, Pi, Pd, Ps, I, xmax, rx, rho, priors,
+                      memo, 0);
     if (st) { orc_free(&c); return st; }
     const size_t rows = (size_t)(N + 1) * c.M;
     double *A = (double *)malloc(rows * sizeof(double));
@@ -518,10 +549,29 @@ int orc_decode(int q, int n, const uint8_t *codebook, int N, double Pi, double P
         if (!(aN > 0.0)) st = ORC_ERR_ZERO_PROB;
         else if (loglik) *loglik = ls + log(aN) - (double)rho * log(g_kappa);
     }
-    if (!st && app) st = orc_backward(&c, B);
-    if (!st && app) st = orc_app(&c, A, B, app, NULL, NULL);
+    if (!st && (app || ext)) st = orc_backward(&c, B);
+    if (!st && (app || ext)) st = orc_app(&c, A, B, app, ext, NULL);
+    if (!st && ext) {
+        for (int i = 0; i < N && !st; ++i) {
+            double *e = ext + (size_t)i * q;
+            double s = 0.0;
+            for (int D = 0; D < q; ++D) s += e[D];
+            if (!(s > 0.0)) st = ORC_ERR_ZERO_PROB;
+            else
+                for (int D = 0; D < q; ++D) e[D] /= s;
+        }
+    }
     free(A); free(B); orc_free(&c);
     return st;
+}
+
+/* Full decode with one codebook: APPs (N*q) and log P(Y). */
+int orc_decode(int q, int n, const uint8_t *codebook, int N, double Pi, double Pd, double Ps,
+               int I, int xmax, const uint8_t *rx, int64_t rho, const double *priors, int memo,
+               double *app, double *loglik)
+{
+    return orc_decode_general(q, n, codebook, 0, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, memo,
+                              app, NULL, loglik);
 }
 
 /*
@@ -533,7 +583,7 @@ int orc_forward_backward(int q, int n, const uint8_t *codebook, int N, double Pi
                          const double *priors, double *A, double *B, double *logc)
 {
     orc_ctx c;
-    int st = orc_init(&c, q, n, codebook, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, 1, 0);
+    int st = orc_init(&c, q, n, codebook, 0, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, 1, 0);
     if (st) { orc_free(&c); return st; }
     double ls = 0.0;
     st = orc_forward(&c, A, &ls);
@@ -572,16 +622,16 @@ int orc_forward_backward(int q, int n, const uint8_t *codebook, int N, double Pi
  *   drift limits held fixed (forward-mode dual numbers through the lattice
  *   and the forward pass);
  *   dlogp_dpriors[i*q + D] = d logP / d Pr{D_i = D} = Q_i(D) / Z_i.
- * Either output may be NULL.
+ * Either output may be NULL.  codebooks / per_symbol as for orc_decode_general.
  */
-int orc_loglik_grad(int q, int n, const uint8_t *codebook, int N, double Pi, double Pd,
-                    double Ps, int I, int xmax, const uint8_t *rx, int64_t rho,
-                    const double *priors, int memo, double *dlogp_dchan, double *dlogp_dpriors,
-                    double *loglik)
+int orc_loglik_grad_general(int q, int n, const uint8_t *codebooks, int per_symbol, int N,
+                            double Pi, double Pd, double Ps, int I, int xmax, const uint8_t *rx,
+                            int64_t rho, const double *priors, int memo, double *dlogp_dchan,
+                            double *dlogp_dpriors, double *loglik)
 {
     orc_ctx c;
-    int st = orc_init(&c, q, n, codebook, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, memo,
-                      dlogp_dchan != NULL);
+    int st = orc_init(&c, q, n, codebooks, per_symbol, N, Pi, Pd, Ps, I, xmax, rx, rho, priors,
+                      memo, dlogp_dchan != NULL);
     if (st) { orc_free(&c); return st; }
     const int M = c.M, Mn = c.Mn;
     const int end = (int)(rho - (int64_t)n * N) + xmax;
@@ -646,4 +696,14 @@ int orc_loglik_grad(int q, int n, const uint8_t *codebook, int N, double Pi, dou
     }
     orc_free(&c);
     return st;
+}
+
+/* log P(Y) and its gradient with one codebook for every symbol. */
+int orc_loglik_grad(int q, int n, const uint8_t *codebook, int N, double Pi, double Pd,
+                    double Ps, int I, int xmax, const uint8_t *rx, int64_t rho,
+                    const double *priors, int memo, double *dlogp_dchan, double *dlogp_dpriors,
+                    double *loglik)
+{
+    return orc_loglik_grad_general(q, n, codebook, 0, N, Pi, Pd, Ps, I, xmax, rx, rho, priors,
+                                   memo, dlogp_dchan, dlogp_dpriors, loglik);
 }

@@ -65,13 +65,25 @@ def frame_bruteforce(codebook, priors, rx, I, Pi, Pd, Ps, xmax):
 
     Sums over every message (q^N) and every split of rx into N consecutive
     pieces of length 0..n(I+1) whose boundary drifts stay within [-xmax, xmax],
-    with per-piece probabilities from `enumerate_channel`.
+    with per-piece probabilities from `enumerate_channel`.  codebook is (q, n),
+    one codebook for every symbol, or (N, q, n), a codebook C_k per symbol
+    (the constituent encodings of Sec. II-A).
     """
-    q, n = codebook.shape
+    codebook = np.asarray(codebook)
     N = priors.shape[0]
+    books = codebook if codebook.ndim == 3 else np.broadcast_to(codebook, (N,) + codebook.shape)
+    q, n = books.shape[1:]
     rho = len(rx)
     ry = tuple(int(b) for b in rx)
-    tables = [enumerate_channel(codebook[d], I, Pi, Pd, Ps) for d in range(q)]
+    cache = {}
+
+    def table(k, d):
+        key = tuple(int(b) for b in books[k][d])
+        if key not in cache:
+            cache[key] = enumerate_channel(books[k][d], I, Pi, Pd, Ps)
+        return cache[key]
+
+    tables = [[table(k, d) for d in range(q)] for k in range(N)]
     maxlen = n * (I + 1)
 
     def p_given_msg(msg):
@@ -92,7 +104,7 @@ def frame_bruteforce(codebook, priors, rx, I, Pi, Pd, Ps, xmax):
                 drift = end - n * (k + 1)
                 if abs(drift) > xmax:
                     continue
-                pr = tables[msg[k]].get(ry[pos:end], 0.0)
+                pr = tables[k][msg[k]].get(ry[pos:end], 0.0)
                 if pr != 0.0:
                     rec(k + 1, end, acc * pr)
 
@@ -146,15 +158,18 @@ def whole_frame_lattice(x, rx, I, Pi, Pd, Ps):
 
 
 def bsc_symbolwise(codebook, priors, rx, Ps):
-    """Pi = Pd = 0: the decoder reduces to symbol-wise MAP on a BSC."""
-    q, n = codebook.shape
+    """Pi = Pd = 0: the decoder reduces to symbol-wise MAP on a BSC.
+    codebook is (q, n) or per-symbol (N, q, n)."""
+    codebook = np.asarray(codebook)
     N = priors.shape[0]
+    books = codebook if codebook.ndim == 3 else np.broadcast_to(codebook, (N,) + codebook.shape)
+    q, n = books.shape[1:]
     app = np.zeros((N, q))
     logp = 0.0
     for i in range(N):
         y = np.asarray(rx[n * i:n * (i + 1)])
         for d in range(q):
-            dh = int(np.sum(y != codebook[d]))
+            dh = int(np.sum(y != books[i][d]))
             app[i, d] = float(priors[i, d]) * Ps ** dh * (1 - Ps) ** (n - dh)
         s = app[i].sum()
         logp += math.log(s)
