@@ -39,6 +39,14 @@ UNIT = "bits/s"
 FRAMES_PER_GPU = 4096
 
 
+def workload_name(frames: int) -> str:
+    """The timed workload, named the same way by both arms of the benchmark."""
+    return (f"mixed-{frames}: N~U[100,4000], (q,n) in "
+            "{(2,4),(8,6),(16,10),(32,8),(64,12)}, Pi=Pd log-U[1e-3,0.1], "
+            "Ps~U[0,0.01], I=2, xmax=ceil(6 sqrt(N n (Pi+Pd))), "
+            "Dirichlet(1) priors")
+
+
 # ---------------------------------------------------------------------------
 # work accounting
 # ---------------------------------------------------------------------------
@@ -368,8 +376,10 @@ def main():
                 "warmup": warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "impl": "reference",
-                "config": {"workload": f"mixed-4096: FP64 CPU oracle on a sample of "
-                                       f"{len(sample)} frames per step"},
+                "config": {"workload": workload_name(FRAMES_PER_GPU),
+                           "frames_per_gpu": FRAMES_PER_GPU,
+                           "reference": f"FP64 CPU oracle on {cores} host threads, a sample of "
+                                        f"{len(sample)} frames per step"},
                 "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                                  "sample": f"workload frames {sample[:8]}{'...' if len(sample) > 8 else ''} "
                                            f"({len(sample)} frames, {bits_tot:.0f} info bits)"},
@@ -545,10 +555,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_gpus, "steps": steps,
             "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"mixed-{args.frames}: N~U[100,4000], (q,n) in "
-                                   "{(2,4),(8,6),(16,10),(32,8),(64,12)}, Pi=Pd log-U[1e-3,0.1], "
-                                   "Ps~U[0,0.01], I=2, xmax=ceil(6 sqrt(N n (Pi+Pd))), "
-                                   "Dirichlet(1) priors; one CUDA-graph batch per GPU",
+            "config": {"workload": workload_name(args.frames),
+                       "launch": "one CUDA-graph batch per GPU",
                        "frames_per_gpu": args.frames, "info_bits_per_gpu_step": bits_per_step,
                        "l2": "inputs and scratch larger than L2 (no flush needed)",
                        "waves": mapdec.mapdec_batch_num_waves(b.b),
