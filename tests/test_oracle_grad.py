@@ -126,3 +126,27 @@ def test_grad_memo_matches_plain():
     b = _grad(fr, memo=False)
     assert a[0] == b[0]
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_channel_grad_vs_oracle_fd_on_gradient_workload_frame():
+    """Frame 0 of the 256-frame gradient workload (N = 2000, q = 32, n = 8,
+    xmax = 120): the dual-number channel gradient against central differences
+    of the oracle's log P (h = 1e-6), and the path-count identity, at full size."""
+    fr = synth.config_frame(4, 0)
+    pr = fr.priors.astype(np.float64)
+    ll, g, _ = oracle.loglik_grad(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax, fr.rx,
+                                  priors=pr, want_priors=False)
+    h = 1e-6
+    noise = 8 * np.finfo(np.float64).eps * abs(ll) / h
+    base = [fr.Pi, fr.Pd, fr.Ps]
+    for k in range(3):
+        up = list(base); up[k] += h
+        dn = list(base); dn[k] -= h
+        fd = (_ll(fr, *up, priors=pr) - _ll(fr, *dn, priors=pr)) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-6, abs=noise), k
+    Pi, Pd = fr.Pi, fr.Pd
+    Pt = 1 - Pi - Pd
+    dd = (g[1] * Pt + fr.tau) / (Pt + Pd)
+    dt = (fr.tau - Pd * dd) / Pt
+    di = (fr.rho - fr.tau + Pd * dd) / Pi
+    assert g[0] == pytest.approx(di - dt, rel=1e-9, abs=1e-7)
