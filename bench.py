@@ -69,6 +69,14 @@ def valid_transitions(fr) -> int:
     return tot
 
 
+def lattice_counts(frames) -> dict:
+    """Lattices per step: evaluated here, one per (rx start p, D), against the
+    paper's gamma grid of one per (i, m', D)."""
+    ev = sum((f.rho + 1) * f.q for f in frames)
+    grid = sum(f.N * (2 * f.xmax + 1) * f.q for f in frames)
+    return {"evaluated": ev, "paper_grid": grid, "ratio": grid / ev if ev else None}
+
+
 def frame_flops(fr) -> dict:
     """Algorithmic FP32 flops per phase for one frame (one FMA = 2 flops)."""
     lat = (fr.rho + 1) * fr.q * lattice_cells(fr.n, fr.I) * (2 * fr.I + 3)
@@ -565,6 +573,7 @@ def main():
                        "gen_seconds": round(gen_s, 1)},
             "roofline": roofline,
             "algorithmic_tflops": total_alg / (ms / 1e3) / 1e12,
+            "lattices_per_step": lattice_counts(frames),
             "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
             "gpu_launches": launches, "clocks": clk}
     if rank == 0:

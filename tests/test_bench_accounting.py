@@ -1,0 +1,46 @@
+"""Host-side work accounting of the benchmark (CPU): the count of valid
+(i, m', j) transitions behind the algorithmic flop figures, checked against a
+plain loop over the paper's state grid (Sec. II-C: drift m' in [-xmax, xmax]
+at symbol i, received length n + delta with delta in [-n, nI], window inside
+[0, rho]), and the lattice counts with and without the position dedupe."""
+import numpy as np
+import pytest
+
+import bench
+from paper_1802_08483_gb300 import synth
+
+
+def _transitions_by_loop(fr):
+    n, x, rho = fr.n, fr.xmax, fr.rho
+    MN = n * (fr.I + 1) + 1
+    count = 0
+    for i in range(fr.N):
+        for m1 in range(-x, x + 1):
+            p = n * i + m1
+            if p < 0 or p > rho:
+                continue
+            for j in range(MN):
+                m2 = m1 + j - n
+                if -x <= m2 <= x and p + j <= rho:
+                    count += 1
+    return count
+
+
+@pytest.mark.parametrize("seed,q,n,N,I,xmax", [
+    (1, 4, 3, 7, 1, 2),      # narrow limits
+    (2, 8, 5, 20, 2, 9),
+    (3, 2, 4, 30, 2, 40),    # limits wider than the frame
+    (4, 16, 6, 12, 3, 5),
+])
+def test_valid_transitions_match_state_grid_loop(seed, q, n, N, I, xmax):
+    rng = np.random.default_rng(seed)
+    fr = synth.make_frame(rng, q, n, N, I, xmax, 0.08, 0.08, 0.01)
+    assert bench.valid_transitions(fr) == _transitions_by_loop(fr)
+
+
+def test_lattice_counts():
+    frames = [synth.config_frame(3, f) for f in range(4)]
+    c = bench.lattice_counts(frames)
+    assert c["evaluated"] == sum((f.rho + 1) * f.q for f in frames)
+    assert c["paper_grid"] == sum(f.N * (2 * f.xmax + 1) * f.q for f in frames)
+    assert c["ratio"] > 1.0
