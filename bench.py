@@ -216,6 +216,26 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def host_cpu() -> str:
+    """Architecture and CPU model of the host (model name, else the Arm part
+    number from /proc/cpuinfo)."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key, _, val = line.partition(":")
+                key = key.strip().lower()
+                if key == "model name":
+                    model = val.strip()
+                    break
+                if key == "cpu part" and not model:
+                    model = "CPU part " + val.strip()
+    except OSError:
+        pass
+    return f"{platform.machine()}, {model}" if model else platform.machine()
+
+
 # ---------------------------------------------------------------------------
 # per-configuration report (--configs): every synthetic configuration in the
 # launch shape it calls for, device-timed, with algorithmic FP32 rates
@@ -388,7 +408,8 @@ def main():
                            "frames_per_gpu": FRAMES_PER_GPU,
                            "reference": f"FP64 CPU oracle on {cores} host threads, a sample of "
                                         f"{len(sample)} frames per step"},
-                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "cpu": host_cpu(),
+                                 "kind": "oracle",
                                  "sample": f"workload frames {sample[:8]}{'...' if len(sample) > 8 else ''} "
                                            f"({len(sample)} frames, {bits_tot:.0f} info bits)"},
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -403,7 +424,8 @@ def main():
         sample = oracle_sample(0, ORACLE_UNITS_PER_CORE_S * cores * args.oracle_seconds / 2,
                                ORACLE_UNITS_PER_CORE_S * 25)
         bits, wall = run_oracle(sample, cores)
-        cpu = {"value": bits / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+        cpu = {"value": bits / wall, "unit": UNIT, "cores": cores, "cpu": host_cpu(),
+               "kind": "oracle",
                "sample": f"{len(sample)} frames of the mixed workload in index order "
                          f"(frames whose oracle cost exceeds ~25 core-s skipped), "
                          f"{bits:.0f} info bits in {wall:.1f} s"}
