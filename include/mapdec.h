@@ -94,6 +94,14 @@ int mapdec_decode(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *p
                   float *app_out, double *loglik_out);
 
 /*
+ * mapdec_decode plus the extrinsic outputs of the frame (see
+ * MAPDEC_BATCH_EXTRINSIC): ext_out N*q floats, row i = E_i(.), sums to 1.
+ * Any output may be NULL.
+ */
+int mapdec_decode_ext(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *priors,
+                      float *app_out, float *ext_out, double *loglik_out);
+
+/*
  * log P(Y) and its gradient (the adjoint path; not in the paper):
  *   dlogp_dchan[0..2] = d logP / d(Pi, Pd, Ps), with Pt = 1 - Pi - Pd and the
  *     drift limits held fixed (FP64);
@@ -177,7 +185,16 @@ enum {
      * the price of computing the transition weights twice.  Results equal
      * the unsegmented run's to rounding order of the APP partial sums.
      */
-    MAPDEC_BATCH_SEGMENTED = 16
+    MAPDEC_BATCH_SEGMENTED = 16,
+    /*
+     * Also produce extrinsic outputs (mapdec_batch_decode_ext): for iterative
+     * decoding with an outer code (Sec. II-A) the inner decoder passes on
+     * what it learned about each symbol from the received sequence and the
+     * other symbols, i.e. eq. (L) without the symbol's own prior:
+     *   E_i(D) = sum_{m', m} alpha_i(m') R(Y[n i + m' .. n(i+1) + m) | C(D)) beta_{i+1}(m),
+     * normalised over D.  The APP is the prior times E_i, renormalised.
+     */
+    MAPDEC_BATCH_EXTRINSIC = 32
 };
 
 typedef struct mapdec_batch mapdec_batch_t;
@@ -238,6 +255,15 @@ int mapdec_batch_status(mapdec_batch_t *b, int *status_per_frame);
  */
 int mapdec_batch_decode(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
                         float *app_all, double *loglik_all);
+
+/*
+ * As mapdec_batch_decode, plus the extrinsic outputs (batch created with
+ * MAPDEC_BATCH_EXTRINSIC, else MAPDEC_ERR_ARG): ext_all like app_all, row i
+ * of frame f = E_i(.) of that frame, summing to 1 (host or device, may be
+ * NULL).  E_i is defined where the prior is 0.
+ */
+int mapdec_batch_decode_ext(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
+                            float *app_all, float *ext_all, double *loglik_all);
 
 /*
  * Gradients for every frame (batch created with MAPDEC_BATCH_GRAD):

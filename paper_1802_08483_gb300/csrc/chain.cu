@@ -10,7 +10,8 @@
 //                Rows are kept exponentially tilted (see below) so that FP32
 //                holds them; the forward chain keeps the exact FP64 record of
 //                every normaliser and tilt and writes log P(Y).
-//   k_finalize : APPs (eq. L, normalised over D), d logP / d prior and the
+//   k_finalize : APPs (eq. L, normalised over D), extrinsic outputs (eq. L
+//                without the symbol's own prior), d logP / d prior and the
 //                FP64 reduction of the channel-parameter gradient
 //                (k_grad_reduce adds the chunks of a frame in order).
 #include <cstdlib>
@@ -511,8 +512,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
             super_symbols(f, tlo + lane, ilo, ihi);
             myrow = (long long)(tlo + lane) * f.S2 + (i - ilo);
         }
-        double z = 0.0;
-        // pass 1: unnormalised sums into app, and z = sum_D prior(D) L^u(D)
+        double z = 0.0, zu = 0.0;
+        // pass 1: unnormalised sums L^u(D) (eq. L without the prior) into app,
+        // z = sum_D prior(D) L^u(D) and, for the extrinsic output, zu = sum_D L^u(D)
         for (int D0 = 0; D0 < q; D0 += 32) {
             const int D = D0 + lane;
             float s = 0.f;
@@ -523,18 +525,24 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
             if (D < q) {
                 f.app[(size_t)i * q + D] = s;
                 z += (double)f.priors[(size_t)i * q + D] * (double)s;
+                zu += (double)s;
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+            zu += __shfl_xor_sync(0xffffffffu, zu, o);
+        }
         if (!(z > 0.0)) { bad = true; continue; }
         const double iz = 1.0 / z;
+        const double izu = 1.0 / zu;  // zu >= z / max prior > 0
         // pass 2: each lane rescales the entries it wrote
         for (int D = lane; D < q; D += 32) {
             const size_t e = (size_t)i * q + D;
             const double lu = (double)f.app[e];
             f.app[e] = (float)((double)f.priors[e] * lu * iz);
             if (f.dpriors) f.dpriors[e] = (float)(lu * iz);
+            if (f.ext) f.ext[e] = (float)(lu * izu);
         }
         if (grad) {
             double Sw = 0.0, Sd = 0.0, Ss = 0.0;

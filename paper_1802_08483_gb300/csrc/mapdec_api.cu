@@ -370,6 +370,7 @@ struct mapdec_batch {
     float *d_priors = nullptr;
     float *d_app = nullptr;
     float *d_dpriors = nullptr;
+    float *d_ext = nullptr;
     double *d_loglik = nullptr;
     double *d_dchan = nullptr;
     int *d_status = nullptr;
@@ -422,6 +423,7 @@ struct mapdec {
     mapdec_batch *b = nullptr;      // batch of one frame, rebuilt when rho changes
     int64_t b_rho = -1;
     bool b_grad = false;
+    bool b_ext = false;
     float *d_rout = nullptr;
     size_t rout_floats = 0;
     ~mapdec() {
@@ -570,6 +572,7 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         b->d_dpriors = (float *)b->dalloc(b->prior_total * 4);
         b->d_dchan = (double *)b->dalloc((size_t)nf * 3 * 8);
     }
+    if (flags & MAPDEC_BATCH_EXTRINSIC) b->d_ext = (float *)b->dalloc(b->prior_total * 4);
     b->d_loglik = (double *)b->dalloc((size_t)nf * 8);
     b->d_status = (int *)b->dalloc((size_t)nf * 4);
     b->d_rxw = (uint32_t *)b->dalloc(b->rxw_total * 4);
@@ -673,6 +676,7 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             f.Rout = nullptr;
             f.app = b->d_app + h.sym_off;
             f.dpriors = b->grad ? b->d_dpriors + h.sym_off : nullptr;
+            f.ext = b->d_ext ? b->d_ext + h.sym_off : nullptr;
             f.loglik = b->d_loglik + i;
             f.dchan = b->grad ? b->d_dchan + 3 * (size_t)i : nullptr;
             f.status = b->d_status + i;
@@ -1202,6 +1206,23 @@ int mapdec_batch_decode(mapdec_batch_t *b, const uint8_t *rx_all, const float *p
     }
 }
 
+int mapdec_batch_decode_ext(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
+                            float *app_all, float *ext_all, double *loglik_all) {
+    if (!b || !rx_all || !b->d_ext) return MAPDEC_ERR_ARG;
+    try {
+        load_inputs(b, rx_all, priors_all);
+        int st = run_batch(b, false);
+        if (st) return st;
+        copy_out(app_all, b->d_app, (size_t)b->prior_total * 4, b->stream);
+        copy_out(ext_all, b->d_ext, (size_t)b->prior_total * 4, b->stream);
+        copy_out(loglik_all, b->d_loglik, (size_t)b->nframes * 8, b->stream);
+        return worst_status(b);
+    } catch (CudaErr &e) {
+        cudaGetLastError();
+        return map_cuda(e.e);
+    }
+}
+
 int mapdec_batch_loglik_grad(mapdec_batch_t *b, const uint8_t *rx_all, const float *priors_all,
                              double *dchan_all, float *dpriors_all, double *loglik_all) {
     if (!b || !rx_all) return MAPDEC_ERR_ARG;
@@ -1312,11 +1333,12 @@ int mapdec_set_stream(mapdec_t *h, void *s) {
     return MAPDEC_OK;
 }
 
-static int ensure_single(mapdec_t *h, int64_t rho, bool grad) {
+static int ensure_single(mapdec_t *h, int64_t rho, bool grad, bool ext = false) {
     const long long tau = (long long)h->n * h->N;
     if (rho < 0) return MAPDEC_ERR_ARG;
     if (std::llabs(rho - tau) > h->xmax) return MAPDEC_ERR_DRIFT_RANGE;
-    if (h->b && h->b_rho == rho && (h->b_grad || !grad)) return MAPDEC_OK;
+    if (h->b && h->b_rho == rho && (h->b_grad || !grad) && (h->b_ext || !ext))
+        return MAPDEC_OK;
     delete h->b;
     h->b = nullptr;
     mapdec_frame_desc_t d;
@@ -1325,12 +1347,14 @@ static int ensure_single(mapdec_t *h, int64_t rho, bool grad) {
     d.codebook = h->codebook.data();
     d.rx_len = rho;
     mapdec_batch_t *b = nullptr;
-    int st = mapdec_batch_create(&b, &d, 1, MAPDEC_BATCH_PLAIN | (grad ? MAPDEC_BATCH_GRAD : 0), 0);
+    int st = mapdec_batch_create(&b, &d, 1, MAPDEC_BATCH_PLAIN | (grad ? MAPDEC_BATCH_GRAD : 0) |
+                                                (ext ? MAPDEC_BATCH_EXTRINSIC : 0), 0);
     if (st) return st;
     b->stream = h->stream;
     h->b = b;
     h->b_rho = rho;
     h->b_grad = grad;
+    h->b_ext = ext;
     return MAPDEC_OK;
 }
 
@@ -1340,6 +1364,15 @@ int mapdec_decode(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *p
     int st = ensure_single(h, rx_len, false);
     if (st) return st;
     return mapdec_batch_decode(h->b, rx ? rx : (const uint8_t *)"", priors, app_out, loglik_out);
+}
+
+int mapdec_decode_ext(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *priors,
+                      float *app_out, float *ext_out, double *loglik_out) {
+    if (!h || (!rx && rx_len > 0)) return MAPDEC_ERR_ARG;
+    int st = ensure_single(h, rx_len, false, true);
+    if (st) return st;
+    return mapdec_batch_decode_ext(h->b, rx ? rx : (const uint8_t *)"", priors, app_out, ext_out,
+                                   loglik_out);
 }
 
 int mapdec_loglik_grad(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const float *priors,

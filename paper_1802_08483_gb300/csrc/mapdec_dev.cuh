@@ -101,6 +101,7 @@ struct FrameDev {
     // outputs
     float *app;      // N*q
     float *dpriors;  // N*q or null
+    float *ext;      // N*q extrinsic outputs, or null
     double *loglik;  // 1
     double *dchan;   // 3 or null
     int *status;     // 1

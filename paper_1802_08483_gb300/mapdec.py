@@ -34,6 +34,7 @@ MAPDEC_BATCH_PLAIN = 2
 MAPDEC_BATCH_GRAD = 4
 MAPDEC_BATCH_TIMING = 8
 MAPDEC_BATCH_SEGMENTED = 16
+MAPDEC_BATCH_EXTRINSIC = 32
 PHASES = ("pack", "forward", "chains", "backward", "finalize")
 
 
@@ -60,6 +61,7 @@ _SIGS = {
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     "mapdec_set_stream": (ctypes.c_int, [_VP, _VP]),
     "mapdec_decode": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
+    "mapdec_decode_ext": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
     "mapdec_loglik_grad": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
     "mapdec_receiver_metric": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
     "mapdec_destroy": (None, [_VP]),
@@ -74,6 +76,7 @@ _SIGS = {
     "mapdec_batch_sync": (ctypes.c_int, [_VP]),
     "mapdec_batch_status": (ctypes.c_int, [_VP, _VP]),
     "mapdec_batch_decode": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "mapdec_batch_decode_ext": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "mapdec_batch_loglik_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "mapdec_batch_set_stream": (ctypes.c_int, [_VP, _VP]),
     "mapdec_batch_destroy": (None, [_VP]),
@@ -171,6 +174,11 @@ def mapdec_decode(h, rx, rx_len, priors, app_out, loglik_out):
                                 _ptr(loglik_out))
 
 
+def mapdec_decode_ext(h, rx, rx_len, priors, app_out, ext_out, loglik_out):
+    return load().mapdec_decode_ext(h, _ptr(rx), int(rx_len), _ptr(priors), _ptr(app_out),
+                                    _ptr(ext_out), _ptr(loglik_out))
+
+
 def mapdec_loglik_grad(h, rx, rx_len, priors, dlogp_dchan, dlogp_dpriors, loglik_out):
     return load().mapdec_loglik_grad(h, _ptr(rx), int(rx_len), _ptr(priors), _ptr(dlogp_dchan),
                                      _ptr(dlogp_dpriors), _ptr(loglik_out))
@@ -251,6 +259,11 @@ def mapdec_batch_decode(b, rx_all, priors_all, app_all, loglik_all):
                                       _ptr(loglik_all))
 
 
+def mapdec_batch_decode_ext(b, rx_all, priors_all, app_all, ext_all, loglik_all):
+    return load().mapdec_batch_decode_ext(b, _ptr(rx_all), _ptr(priors_all), _ptr(app_all),
+                                          _ptr(ext_all), _ptr(loglik_all))
+
+
 def mapdec_batch_loglik_grad(b, rx_all, priors_all, dchan_all, dpriors_all, loglik_all):
     return load().mapdec_batch_loglik_grad(b, _ptr(rx_all), _ptr(priors_all), _ptr(dchan_all),
                                            _ptr(dpriors_all), _ptr(loglik_all))
@@ -329,6 +342,17 @@ class Decoder:
         _check(mapdec_decode(self.h, rx, rx.size, pr, app, ll), "mapdec_decode")
         return app, float(ll[0])
 
+    def decode_ext(self, rx, priors=None):
+        """(APPs, extrinsic outputs, log P): eq. (L) with and without each
+        symbol's own prior, both normalised over D."""
+        rx = np.ascontiguousarray(rx, dtype=np.uint8)
+        pr = None if priors is None else np.ascontiguousarray(priors, dtype=np.float32)
+        app = np.zeros((self.N, self.q), np.float32)
+        ext = np.zeros((self.N, self.q), np.float32)
+        ll = np.zeros(1, np.float64)
+        _check(mapdec_decode_ext(self.h, rx, rx.size, pr, app, ext, ll), "mapdec_decode_ext")
+        return app, ext, float(ll[0])
+
     def loglik_grad(self, rx, priors=None):
         rx = np.ascontiguousarray(rx, dtype=np.uint8)
         pr = None if priors is None else np.ascontiguousarray(priors, dtype=np.float32)
@@ -383,6 +407,15 @@ class Batch:
         ll = np.zeros(self.nf, np.float64)
         st = mapdec_batch_decode(self.b, rx_all, priors_all, app, ll)
         return st, app, ll
+
+    def decode_ext(self, rx_all, priors_all):
+        """Batch created with MAPDEC_BATCH_EXTRINSIC: (status, APPs, extrinsic
+        outputs, log-likelihoods), APPs and extrinsic outputs concatenated."""
+        app = np.zeros(self.prior_total, np.float32)
+        ext = np.zeros(self.prior_total, np.float32)
+        ll = np.zeros(self.nf, np.float64)
+        st = mapdec_batch_decode_ext(self.b, rx_all, priors_all, app, ext, ll)
+        return st, app, ext, ll
 
     def loglik_grad(self, rx_all, priors_all):
         dchan = np.zeros(3 * self.nf, np.float64)
