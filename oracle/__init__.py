@@ -12,8 +12,9 @@ enumeration of channel events, closed forms and invariants (see
 
 ``decode_ext`` and ``loglik_grad`` also take per-symbol codebooks (the
 constituent encodings C_i of Sec. II-A) and ``decode_ext`` returns the
-extrinsic outputs used in iterative decoding; the CUDA decoder implements
-neither yet, so these serve as the reference for that next step.
+extrinsic outputs used in iterative decoding.  The CUDA decoder produces the
+extrinsic outputs too (checked against ``decode_ext``); per-symbol codebooks
+exist only here so far, as the reference for that next step.
 """
 from __future__ import annotations
 
