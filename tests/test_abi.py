@@ -60,3 +60,14 @@ def test_no_gpu_fails_loudly(lib):
     with pytest.raises(mapdec.MapDecError) as e:
         mapdec.mapdec_create(2, 2, cb, 4, 0.01, 0.01, 0.0, 1, 4)
     assert e.value.status == mapdec.MAPDEC_ERR_CUDA
+
+
+def test_constants_match_header():
+    """Every status code and batch flag of the header has the same value in the
+    binding (the binding restates them for ctypes callers)."""
+    import re
+    txt = re.sub(r"/\*.*?\*/", "", open(mapdec.HEADER).read(), flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(MAPDEC_[A-Z0-9_]+)\s*=\s*(\d+)", txt))
+    assert "MAPDEC_BATCH_EXTRINSIC" in consts and "MAPDEC_ERR_ARG" in consts
+    for k, v in consts.items():
+        assert getattr(mapdec, k, None) == v, f"{k}: header {v}, binding {getattr(mapdec, k, None)}"
