@@ -8,6 +8,8 @@ computation runs in libmapdec.so.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 import torch
 
@@ -19,6 +21,11 @@ def _chan_tuple(chan):
     return float(c[0]), float(c[1]), float(c[2])
 
 
+def _same_channel(got, want) -> bool:
+    """chan holds the channel the decoder was planned for (to float32 rounding)."""
+    return all(math.isclose(a, b, rel_tol=1e-6, abs_tol=1e-12) for a, b in zip(got, want))
+
+
 class FrameLogLik(torch.autograd.Function):
     """log P(Y) of one frame as a function of (priors (N, q), chan = [Pi, Pd, Ps]).
 
@@ -28,8 +35,7 @@ class FrameLogLik(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, priors, chan, decoder, rx):
-        pi, pd, ps = _chan_tuple(chan)
-        if (pi, pd, ps) != (decoder.Pi, decoder.Pd, decoder.Ps):
+        if not _same_channel(_chan_tuple(chan), (decoder.Pi, decoder.Pd, decoder.Ps)):
             raise ValueError("chan differs from the decoder's channel parameters")
         pr = priors.detach().to("cpu", torch.float32).contiguous().numpy()
         ll, dchan, dpri = decoder.loglik_grad(np.asarray(rx, np.uint8), pr)
@@ -54,6 +60,13 @@ class BatchLogLik(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, priors_all, chan, batch, rx_all):
+        ch = chan.detach().to("cpu", torch.float64).reshape(-1)
+        if ch.numel() != 3 * len(batch.frames):
+            raise ValueError(f"chan holds {ch.numel()} values for {len(batch.frames)} frames")
+        for k, f in enumerate(batch.frames):
+            got = (float(ch[3 * k]), float(ch[3 * k + 1]), float(ch[3 * k + 2]))
+            if not _same_channel(got, (f.Pi, f.Pd, f.Ps)):
+                raise ValueError(f"chan of frame {k} differs from the batch's channel parameters")
         st, dchan, dpri, ll = batch.loglik_grad(np.asarray(rx_all, np.uint8),
                                                 priors_all.detach().to("cpu", torch.float32)
                                                 .contiguous().numpy())
