@@ -69,6 +69,19 @@ def valid_transitions(fr) -> int:
     return tot
 
 
+def write_jsonl(path: str, frames, frame_offset: int, loglik, status, summary: dict) -> None:
+    """Per-frame results of a run, one JSON object per line (frame index in the
+    workload, shape, channel, log P(Y), status), then one summary object."""
+    with open(path, "w") as fh:
+        for k, f in enumerate(frames):
+            fh.write(json.dumps({"frame": frame_offset + k, "q": int(f.q), "n": int(f.n),
+                                 "N": int(f.N), "I": int(f.I), "xmax": int(f.xmax),
+                                 "rho": int(f.rho), "Pi": float(f.Pi), "Pd": float(f.Pd),
+                                 "Ps": float(f.Ps), "loglik": float(loglik[k]),
+                                 "status": int(status[k])}) + "\n")
+        fh.write(json.dumps(dict({"summary": True}, **summary)) + "\n")
+
+
 def lattice_counts(frames) -> dict:
     """Lattices per step: evaluated here, one per (rx start p, D), against the
     paper's gamma grid of one per (i, m', D)."""
@@ -371,6 +384,9 @@ def main():
                          "(comma list; default 1,2,4,5)")
     ap.add_argument("--tuning", default=DEFAULT_TUNING,
                     help="tuning table (JSON written by paper_1802_08483_gb300.tune); '' = none")
+    ap.add_argument("--log-jsonl", default="",
+                    help="write per-frame log P(Y) and status plus a summary to this JSONL file "
+                         "(rank r > 0 appends .rank<r>)")
     ap.add_argument("--mem-budget-gb", type=float, default=0.0,
                     help="device scratch budget (0 = 60%% of free memory); frames beyond it "
                          "are decoded in further waves")
@@ -600,6 +616,11 @@ def main():
             "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         print(json.dumps(line))
+    if args.log_jsonl:
+        path = args.log_jsonl if rank == 0 else f"{args.log_jsonl}.rank{rank}"
+        write_jsonl(path, frames, frame_offset, ll0, mapdec.mapdec_batch_status(b.b, b.nf),
+                    {"rank": rank, "ms_per_step": ms, "job_bits_per_s": value,
+                     "phase_ms": line["roofline"]["phase_ms"], "steps": steps})
     b.close()
     if world > 1:
         dist.destroy_process_group()

@@ -44,3 +44,16 @@ def test_lattice_counts():
     assert c["evaluated"] == sum((f.rho + 1) * f.q for f in frames)
     assert c["paper_grid"] == sum(f.N * (2 * f.xmax + 1) * f.q for f in frames)
     assert c["ratio"] > 1.0
+
+
+def test_write_jsonl(tmp_path):
+    import json
+    frames = [synth.config_frame(3, f) for f in range(3)]
+    path = tmp_path / "run.jsonl"
+    bench.write_jsonl(str(path), frames, 10, [-1.5, -2.5, -3.5], [0, 0, 3],
+                      {"ms_per_step": 1.0})
+    rows = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(rows) == 4 and rows[-1]["summary"] is True
+    assert [r["frame"] for r in rows[:3]] == [10, 11, 12]
+    assert rows[2]["status"] == 3 and rows[1]["loglik"] == -2.5
+    assert rows[0]["rho"] == frames[0].rho and rows[0]["q"] == frames[0].q
