@@ -24,6 +24,7 @@ import subprocess
 import sys
 import threading
 import time
+from typing import Optional
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_TUNING = os.path.join(ROOT, "paper_1802_08483_gb300", "tuning", "gb300_mixed4096.json")
@@ -220,6 +221,20 @@ def kernel_sources_sha1() -> str:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def phase_traffic(phase: str, path: str = "") -> Optional[int]:
+    """DRAM bytes per step of one phase from the committed launch-list capture,
+    or None when the kernel sources changed since the counters were taken (or
+    the capture is missing)."""
+    try:
+        with open(path or os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            prof = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if prof.get("csrc_sha1") != kernel_sources_sha1():
+        return None
+    return prof.get(phase)
 
 
 def host_cores() -> int:
@@ -539,15 +554,7 @@ def main():
     dom_name = names[dom]
     dom_flops = flops.get(dom_name, 0)
     achieved = dom_flops / (phase_ms[dom] / 1e3) / 1e12 if phase_ms[dom] > 0 else 0.0
-    # DRAM bytes of the phase per step from the committed launch-list capture;
-    # null when the kernel sources changed since the counters were taken
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        if prof.get("csrc_sha1") == kernel_sources_sha1():
-            traffic = prof.get(dom_name)
-    except (OSError, ValueError):
-        pass
+    traffic = phase_traffic(dom_name)
     try:
         probe = mapdec.mapdec_fp32_fma_peak(stream.cuda_stream)
     except mapdec.MapDecError:

@@ -57,3 +57,16 @@ def test_write_jsonl(tmp_path):
     assert [r["frame"] for r in rows[:3]] == [10, 11, 12]
     assert rows[2]["status"] == 3 and rows[1]["loglik"] == -2.5
     assert rows[0]["rho"] == frames[0].rho and rows[0]["q"] == frames[0].q
+
+
+def test_phase_traffic_follows_the_source_hash(tmp_path):
+    """The committed DRAM bytes are reported only for the kernel sources they
+    were taken on."""
+    import json
+    good = tmp_path / "good.json"
+    good.write_text(json.dumps({"csrc_sha1": bench.kernel_sources_sha1(), "backward": 123}))
+    stale = tmp_path / "stale.json"
+    stale.write_text(json.dumps({"csrc_sha1": "0" * 40, "backward": 123}))
+    assert bench.phase_traffic("backward", str(good)) == 123
+    assert bench.phase_traffic("backward", str(stale)) is None
+    assert bench.phase_traffic("backward", str(tmp_path / "missing.json")) is None
