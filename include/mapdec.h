@@ -16,7 +16,10 @@
  *       normalised over D for every symbol;
  *   (4) the frame log-likelihood log P(Y) = sum_i log c_i + log alpha_N(rho-tau),
  *       c_i the forward normalisers of eq. (alpha_norm).
- * Gradients of log P(Y) (not in the paper) are provided by an adjoint path.
+ * Gradients of log P(Y) (not in the paper) are provided by an adjoint path,
+ * and extrinsic outputs for iterative decoding with an outer code (Sec. II-A:
+ * eq. (L) without each symbol's own prior) by mapdec_decode_ext and
+ * mapdec_batch_decode_ext.
  *
  * Conventions shared by every entry point
  *   - Drift states m lie in [-xmax, xmax] at symbol boundaries; the drift
@@ -34,7 +37,8 @@
  *   - Every data pointer may be host or device memory (detected per call).
  *     The caller owns all buffers; a handle owns its device scratch.
  *     Work is issued on the handle's stream.  mapdec_decode,
- *     mapdec_loglik_grad, mapdec_receiver_metric, mapdec_batch_decode and
+ *     mapdec_decode_ext, mapdec_loglik_grad, mapdec_receiver_metric,
+ *     mapdec_batch_decode, mapdec_batch_decode_ext and
  *     mapdec_batch_loglik_grad return after that stream has drained, so
  *     their status covers the whole computation; mapdec_batch_run is
  *     asynchronous.
