@@ -76,7 +76,12 @@ typedef struct mapdec mapdec_t;
  *   codebook: q*n bytes (host or device), distinct rows;
  *   N >= 1 symbols per frame; channel Pi, Pd, Ps with Pi, Pd, Ps >= 0,
  *   Pi + Pd < 1, Ps <= 1; insertion cap I >= 1; drift limit xmax >= 0.
- * Allocates device scratch sized for the largest received length tau + xmax.
+ * Plans the tiles and allocates the device scratch of the decode path once,
+ * for the largest admissible received length rho_max = tau + xmax (tau = n*N);
+ * mapdec_decode and mapdec_decode_ext then reuse it for every received length
+ * in [tau - xmax, tau + xmax] without allocating.  The gradient path's scratch
+ * is allocated by the first mapdec_loglik_grad call, and the output buffer of
+ * mapdec_receiver_metric by its first call, each once for rho_max.
  * On success *out holds the handle (destroy with mapdec_destroy).
  */
 int mapdec_create(mapdec_t **out, int q, int n, const uint8_t *codebook, int N, double Pi,

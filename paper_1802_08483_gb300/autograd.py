@@ -1,10 +1,13 @@
 """torch.autograd.Function wrappers around the decoder's adjoint path.
 
-forward() calls mapdec_loglik_grad / mapdec_batch_loglik_grad (the CUDA
-kernels compute log P(Y) together with d logP / d(Pi, Pd, Ps) and
-d logP / d prior) and saves the gradients; backward() scales them by the
-incoming gradient.  PyTorch only moves the tensors; every step of the
-computation runs in libmapdec.so.
+forward() runs the decoder on the priors where they live (CUDA priors stay on
+the device; the call is issued on torch's current stream).  When an input
+needs a gradient it calls mapdec_loglik_grad / mapdec_batch_loglik_grad, whose
+CUDA kernels compute log P(Y) together with d logP / d(Pi, Pd, Ps) and
+d logP / d prior, and saves the gradients; otherwise it runs the decode path
+alone for log P(Y).  backward() scales the saved gradients by the incoming
+gradient.  PyTorch only moves the tensors; every step of the computation runs
+in libmapdec.so.
 """
 from __future__ import annotations
 
@@ -26,6 +29,13 @@ def _same_channel(got, want) -> bool:
     return all(math.isclose(a, b, rel_tol=1e-6, abs_tol=1e-12) for a, b in zip(got, want))
 
 
+def _on_current_stream(handle, device):
+    """Issue the handle's work on torch's current stream of a CUDA device, so
+    that it is ordered after the kernels that produced its inputs."""
+    if device.type == "cuda":
+        handle.set_stream(torch.cuda.current_stream(device).cuda_stream)
+
+
 class FrameLogLik(torch.autograd.Function):
     """log P(Y) of one frame as a function of (priors (N, q), chan = [Pi, Pd, Ps]).
 
@@ -37,12 +47,19 @@ class FrameLogLik(torch.autograd.Function):
     def forward(ctx, priors, chan, decoder, rx):
         if not _same_channel(_chan_tuple(chan), (decoder.Pi, decoder.Pd, decoder.Ps)):
             raise ValueError("chan differs from the decoder's channel parameters")
-        pr = priors.detach().to("cpu", torch.float32).contiguous().numpy()
-        ll, dchan, dpri = decoder.loglik_grad(np.asarray(rx, np.uint8), pr)
-        ctx.save_for_backward(torch.from_numpy(np.asarray(dpri, np.float32)).to(priors.device),
-                              torch.from_numpy(np.asarray(dchan, np.float64)).to(chan.device))
+        dev = priors.device
+        pr = priors.detach().to(torch.float32).contiguous()
+        ll = torch.zeros(1, dtype=torch.float64, device=dev)
+        _on_current_stream(decoder, dev)
+        if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
+            dpri = torch.empty_like(pr)
+            dchan = torch.zeros(3, dtype=torch.float64, device=dev)
+            decoder.loglik_grad_into(rx, pr, dchan, dpri, ll)
+            ctx.save_for_backward(dpri, dchan.to(chan.device))
+        else:
+            decoder.loglik_into(rx, pr, ll)
         ctx.dtypes = (priors.dtype, chan.dtype)
-        return torch.tensor(ll, dtype=torch.float64, device=priors.device)
+        return ll[0]
 
     @staticmethod
     def backward(ctx, grad_out):
@@ -67,17 +84,27 @@ class BatchLogLik(torch.autograd.Function):
             got = (float(ch[3 * k]), float(ch[3 * k + 1]), float(ch[3 * k + 2]))
             if not _same_channel(got, (f.Pi, f.Pd, f.Ps)):
                 raise ValueError(f"chan of frame {k} differs from the batch's channel parameters")
-        st, dchan, dpri, ll = batch.loglik_grad(np.asarray(rx_all, np.uint8),
-                                                priors_all.detach().to("cpu", torch.float32)
-                                                .contiguous().numpy())
-        if st != 0:
-            raise mapdec.MapDecError(st, "mapdec_batch_loglik_grad")
-        ctx.save_for_backward(torch.from_numpy(dpri).to(priors_all.device),
-                              torch.from_numpy(dchan).to(chan.device))
+        dev = priors_all.device
+        pr = priors_all.detach().to(torch.float32).contiguous()
+        nf = len(batch.frames)
+        ll = torch.zeros(nf, dtype=torch.float64, device=dev)
+        rx = np.ascontiguousarray(rx_all, np.uint8)
+        _on_current_stream(batch, dev)
+        if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
+            dpri = torch.empty_like(pr)
+            dchan = torch.zeros(nf, 3, dtype=torch.float64, device=dev)
+            st = batch.loglik_grad_into(rx, pr, dchan, dpri, ll)
+            if st != 0:
+                raise mapdec.MapDecError(st, "mapdec_batch_loglik_grad")
+            ctx.save_for_backward(dpri, dchan.to(chan.device))
+        else:
+            st = batch.loglik_into(rx, pr, ll)
+            if st != 0:
+                raise mapdec.MapDecError(st, "mapdec_batch_decode")
         ctx.sym_off = batch.sym_off.copy()
         ctx.sizes = [f.N * f.q for f in batch.frames]
         ctx.dtypes = (priors_all.dtype, chan.dtype)
-        return torch.from_numpy(ll).to(priors_all.device)
+        return ll
 
     @staticmethod
     def backward(ctx, grad_out):
@@ -86,8 +113,9 @@ class BatchLogLik(torch.autograd.Function):
         gp = None
         if ctx.needs_input_grad[0]:
             scale = torch.empty(dpri.numel(), dtype=torch.float64, device=dpri.device)
+            gd = g.to(dpri.device)
             for k, (o, sz) in enumerate(zip(ctx.sym_off, ctx.sizes)):
-                scale[int(o):int(o) + sz] = g[k]
+                scale[int(o):int(o) + sz] = gd[k]
             gp = (dpri.to(torch.float64) * scale).to(ctx.dtypes[0])
         gc = (dchan * g.to(dchan.device)[:, None]).to(ctx.dtypes[1]) \
             if ctx.needs_input_grad[1] else None

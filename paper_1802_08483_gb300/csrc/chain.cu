@@ -617,24 +617,27 @@ size_t chain_smem_bytes(const FrameDev &f) {
 cudaError_t launch_chain(const FrameDev *frames, const Work *work, int nwork, size_t smem,
                          int threads, cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;
-    // Raise the opt-in limit once to the device maximum: graphs hold chain launches
-    // of several waves with different sizes, and every one must stay valid.
-    static int max_dyn = -1;
-    if (max_dyn < 0) {
+    // Raise the opt-in limit to the device maximum, once per device (the
+    // attribute is per device): graphs hold chain launches of several waves
+    // with different sizes, and every one must stay valid.
+    static std::atomic<int> max_dyn[64];  // 0 = not yet set on that device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int lim = (dev >= 0 && dev < 64) ? max_dyn[dev].load(std::memory_order_acquire) : 0;
+    if (lim <= 0) {
         cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, k_chain);
+        e = cudaFuncGetAttributes(&fa, k_chain);
         if (e != cudaSuccess) return e;
-        int dev = 0, optin = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess)
-            e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        int optin = 0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return e;
-        const int lim = optin - (int)fa.sharedSizeBytes;
+        lim = optin - (int)fa.sharedSizeBytes;
         e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (e != cudaSuccess) return e;
-        max_dyn = lim;
+        if (dev >= 0 && dev < 64) max_dyn[dev].store(lim, std::memory_order_release);
     }
-    if ((long long)smem > max_dyn) return cudaErrorInvalidValue;
+    if ((long long)smem > lim) return cudaErrorInvalidValue;
     if (threads != 128 && threads != 256 && threads != 512) threads = kChainThreads;
     k_chain<<<nwork, threads, smem, st>>>(frames, work);
     return cudaGetLastError();

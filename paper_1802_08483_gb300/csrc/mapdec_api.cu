@@ -415,19 +415,22 @@ struct mapdec_batch {
     }
 };
 
+// Single-frame handle.  Its batches of one frame are planned and allocated
+// once for the largest admissible received length rho_max = tau + xmax; a call
+// with any rho in [tau - xmax, tau + xmax] only rewrites the frame descriptor
+// and the producers' work counts (the work lists are prefixes of rho_max's).
 struct mapdec {
     int q, n, N, I, xmax;
     double Pi, Pd, Ps;
     std::vector<uint8_t> codebook;  // host copy
     cudaStream_t stream = nullptr;
-    mapdec_batch *b = nullptr;      // batch of one frame, rebuilt when rho changes
-    int64_t b_rho = -1;
-    bool b_grad = false;
-    bool b_ext = false;
-    float *d_rout = nullptr;
-    size_t rout_floats = 0;
+    int64_t rho_max = 0;
+    mapdec_batch *b = nullptr;      // decode (APPs, extrinsic outputs), made by mapdec_create
+    mapdec_batch *bg = nullptr;     // gradient mode, made by the first mapdec_loglik_grad
+    float *d_rout = nullptr;        // receiver-metric dump, (rho_max+1)*q*MN floats, first use
     ~mapdec() {
         delete b;
+        delete bg;
         if (d_rout) cudaFree(d_rout);
     }
 };
@@ -1319,9 +1322,20 @@ int mapdec_create(mapdec_t **out, int q, int n, const uint8_t *codebook, int N, 
     if (!h) return MAPDEC_ERR_NOMEM;
     h->q = q; h->n = n; h->N = N; h->I = I; h->xmax = xmax;
     h->Pi = Pi; h->Pd = Pd; h->Ps = Ps;
+    h->rho_max = (int64_t)n * N + xmax;
     h->codebook.resize((size_t)q * n);
     for (int d = 0; d < q; ++d)
         for (int r = 0; r < n; ++r) h->codebook[(size_t)d * n + r] = (cw[d] >> r) & 1u;
+    mapdec_frame_desc_t d;
+    d.q = q; d.n = n; d.N = N; d.I = I; d.xmax = xmax;
+    d.Pi = Pi; d.Pd = Pd; d.Ps = Ps;
+    d.codebook = h->codebook.data();
+    d.rx_len = h->rho_max;
+    st = mapdec_batch_create(&h->b, &d, 1, MAPDEC_BATCH_PLAIN | MAPDEC_BATCH_EXTRINSIC, 0);
+    if (st) {
+        delete h;
+        return st;
+    }
     *out = h;
     return MAPDEC_OK;
 }
@@ -1330,31 +1344,55 @@ int mapdec_set_stream(mapdec_t *h, void *s) {
     if (!h) return MAPDEC_ERR_ARG;
     h->stream = (cudaStream_t)s;
     if (h->b) h->b->stream = h->stream;
+    if (h->bg) h->bg->stream = h->stream;
     return MAPDEC_OK;
 }
+
+namespace {
+
+// Point the one-frame batch of a handle at received length rho (allocated for
+// rho_max >= rho): the descriptor gets rho and its tile counts, the producer
+// launches their prefix of the work lists, and the extrinsic output pointer is
+// set only when asked for.  Nothing is allocated.
+void retarget_single(mapdec_batch *b, int64_t rho, bool ext) {
+    FrameHost &h = b->fr[0];
+    FrameDev &f = h.dev;
+    h.d.rx_len = rho;
+    f.rho = rho;
+    f.T = (int)((rho + 1 + f.P - 1) / f.P);
+    f.T2 = (f.T + f.nsub - 1) / f.nsub;
+    f.ext = ext ? b->d_ext : nullptr;
+    b->rx_total = rho;
+    Wave &w = b->waves[0];
+    for (auto &c : w.cls) {
+        c.nfwd = f.T;
+        c.nbwd = f.T2;
+    }
+    CK(cudaMemcpyAsync(w.d_frames, &f, sizeof(FrameDev), cudaMemcpyHostToDevice, b->stream));
+}
+
+}  // namespace
 
 static int ensure_single(mapdec_t *h, int64_t rho, bool grad, bool ext = false) {
     const long long tau = (long long)h->n * h->N;
     if (rho < 0) return MAPDEC_ERR_ARG;
     if (std::llabs(rho - tau) > h->xmax) return MAPDEC_ERR_DRIFT_RANGE;
-    if (h->b && h->b_rho == rho && (h->b_grad || !grad) && (h->b_ext || !ext))
-        return MAPDEC_OK;
-    delete h->b;
-    h->b = nullptr;
-    mapdec_frame_desc_t d;
-    d.q = h->q; d.n = h->n; d.N = h->N; d.I = h->I; d.xmax = h->xmax;
-    d.Pi = h->Pi; d.Pd = h->Pd; d.Ps = h->Ps;
-    d.codebook = h->codebook.data();
-    d.rx_len = rho;
-    mapdec_batch_t *b = nullptr;
-    int st = mapdec_batch_create(&b, &d, 1, MAPDEC_BATCH_PLAIN | (grad ? MAPDEC_BATCH_GRAD : 0) |
-                                                (ext ? MAPDEC_BATCH_EXTRINSIC : 0), 0);
-    if (st) return st;
-    b->stream = h->stream;
-    h->b = b;
-    h->b_rho = rho;
-    h->b_grad = grad;
-    h->b_ext = ext;
+    if (grad && !h->bg) {
+        mapdec_frame_desc_t d;
+        d.q = h->q; d.n = h->n; d.N = h->N; d.I = h->I; d.xmax = h->xmax;
+        d.Pi = h->Pi; d.Pd = h->Pd; d.Ps = h->Ps;
+        d.codebook = h->codebook.data();
+        d.rx_len = h->rho_max;
+        int st = mapdec_batch_create(&h->bg, &d, 1, MAPDEC_BATCH_PLAIN | MAPDEC_BATCH_GRAD, 0);
+        if (st) return st;
+        h->bg->stream = h->stream;
+    }
+    try {
+        retarget_single(grad ? h->bg : h->b, rho, ext);
+    } catch (CudaErr &e) {
+        cudaGetLastError();
+        return map_cuda(e.e);
+    }
     return MAPDEC_OK;
 }
 
@@ -1381,7 +1419,7 @@ int mapdec_loglik_grad(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const flo
     if (!(h->Pd > 0) || !((1.0 - h->Pi - h->Pd) * (1.0 - h->Ps) > 0)) return MAPDEC_ERR_UNSUPPORTED;
     int st = ensure_single(h, rx_len, true);
     if (st) return st;
-    return mapdec_batch_loglik_grad(h->b, rx ? rx : (const uint8_t *)"", priors, dlogp_dchan,
+    return mapdec_batch_loglik_grad(h->bg, rx ? rx : (const uint8_t *)"", priors, dlogp_dchan,
                                     dlogp_dpriors, loglik_out);
 }
 
@@ -1393,21 +1431,16 @@ int mapdec_receiver_metric(mapdec_t *h, const uint8_t *rx, int64_t rx_len, float
     try {
         load_inputs(b, rx ? rx : (const uint8_t *)"", nullptr);
         const FrameHost &fh = b->fr[0];
+        if (!h->d_rout)
+            CK(cudaMalloc(&h->d_rout, (size_t)(h->rho_max + 1) * h->q * fh.dev.MN * 4));
         const size_t nfl = (size_t)(rx_len + 1) * h->q * fh.dev.MN;
-        if (h->rout_floats < nfl) {
-            if (h->d_rout) cudaFree(h->d_rout);
-            h->d_rout = nullptr;
-            CK(cudaMalloc(&h->d_rout, nfl * 4));
-            h->rout_floats = nfl;
-        }
         Wave &w = b->waves[0];
         FrameDev f = fh.dev;
         f.Rout = h->d_rout;
         CK(cudaMemcpyAsync(w.d_frames, &f, sizeof(FrameDev), cudaMemcpyHostToDevice, b->stream));
         CK(launch_pack(w.d_frames, w.d_rxptr, w.d_rxwptr, 1, w.max_words, b->stream));
         CK(launch_rmetric(h->n, h->I, w.d_frames, (long long)(rx_len + 1) * h->q, b->stream));
-        FrameDev f0 = fh.dev;
-        CK(cudaMemcpyAsync(w.d_frames, &f0, sizeof(FrameDev), cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(w.d_frames, &fh.dev, sizeof(FrameDev), cudaMemcpyHostToDevice, b->stream));
         copy_out(R_out, h->d_rout, nfl * 4, b->stream);
         CK(cudaStreamSynchronize(b->stream));
         return MAPDEC_OK;

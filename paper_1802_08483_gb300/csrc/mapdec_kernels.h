@@ -1,6 +1,7 @@
 // Host-side declarations of the kernel launchers (internal to libmapdec.so).
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -8,6 +9,24 @@
 #include "mapdec_dev.cuh"
 
 namespace mdk {
+
+// Raise a kernel's dynamic shared-memory opt-in to `bytes` on the current
+// device, once per device: the attribute is held per device, so a process that
+// launches on several GPUs sets it on each.  `done` has one bit per device
+// (devices 0..63; beyond that the attribute is set on every call).  Safe to
+// call from several threads: concurrent first calls may both set the same
+// value, which is harmless.
+template <typename Kern>
+cudaError_t smem_optin_once(Kern kern, int bytes, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // Producers dispatched on (n, I); pairs without a compiled specialisation run
 // the run-time lattice.  smem = dynamic shared bytes (see *_smem_bytes).

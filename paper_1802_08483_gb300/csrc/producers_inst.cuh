@@ -15,13 +15,9 @@ cudaError_t launch_fwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem,
         if constexpr (IB >= 3) return k_fwd_occ2<NB, IB>;
         else return k_fwd<NB, IB>;
     }();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxDynSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_optin_once(kern, kMaxDynSmem, attr);
+    if (e != cudaSuccess) return e;
     if (nw <= 0) return cudaSuccess;
     kern<<<nw, kThreads, smem, st>>>(fr, w);
     return cudaGetLastError();
@@ -29,14 +25,9 @@ cudaError_t launch_fwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem,
 
 template <int NB, int IB, bool GRAD>
 cudaError_t launch_bwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_bwd<NB, IB, GRAD>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxDynSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_optin_once(k_bwd<NB, IB, GRAD>, kMaxDynSmem, attr);
+    if (e != cudaSuccess) return e;
     if (nw <= 0) return cudaSuccess;
     k_bwd<NB, IB, GRAD><<<nw, kThreads, smem, st>>>(fr, w);
     return cudaGetLastError();

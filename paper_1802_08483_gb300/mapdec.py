@@ -362,6 +362,22 @@ class Decoder:
         _check(mapdec_loglik_grad(self.h, rx, rx.size, pr, dchan, dpri, ll), "mapdec_loglik_grad")
         return float(ll[0]), dchan, dpri
 
+    def loglik_into(self, rx, priors, ll_out):
+        """log P(Y) alone (no APPs copied out) into ll_out: 1 double, host or
+        device.  priors: a contiguous float32 array or tensor (host or device)
+        or None."""
+        rx = np.ascontiguousarray(rx, dtype=np.uint8)
+        _check(mapdec_decode(self.h, rx, rx.size, priors, None, ll_out), "mapdec_decode")
+
+    def loglik_grad_into(self, rx, priors, dchan_out, dpri_out, ll_out):
+        """The adjoint path into caller-owned buffers (host or device)."""
+        rx = np.ascontiguousarray(rx, dtype=np.uint8)
+        _check(mapdec_loglik_grad(self.h, rx, rx.size, priors, dchan_out, dpri_out, ll_out),
+               "mapdec_loglik_grad")
+
+    def set_stream(self, stream):
+        mapdec_set_stream(self.h, stream)
+
     def receiver_metric(self, rx, MN):
         rx = np.ascontiguousarray(rx, dtype=np.uint8)
         R = np.zeros((rx.size + 1, self.q, MN), np.float32)
@@ -416,6 +432,18 @@ class Batch:
         ll = np.zeros(self.nf, np.float64)
         st = mapdec_batch_decode_ext(self.b, rx_all, priors_all, app, ext, ll)
         return st, app, ext, ll
+
+    def loglik_into(self, rx_all, priors_all, ll_out):
+        """Per-frame log P(Y) alone (no APPs copied out) into ll_out (host or
+        device); returns the worst frame status."""
+        return mapdec_batch_decode(self.b, rx_all, priors_all, None, ll_out)
+
+    def loglik_grad_into(self, rx_all, priors_all, dchan_out, dpri_out, ll_out):
+        """The adjoint path into caller-owned buffers (host or device)."""
+        return mapdec_batch_loglik_grad(self.b, rx_all, priors_all, dchan_out, dpri_out, ll_out)
+
+    def set_stream(self, stream):
+        mapdec_batch_set_stream(self.b, stream)
 
     def loglik_grad(self, rx_all, priors_all):
         dchan = np.zeros(3 * self.nf, np.float64)

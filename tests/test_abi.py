@@ -43,9 +43,24 @@ def test_header_documents_every_entry_point():
 
 
 def test_library_does_not_link_oracle(lib):
-    # the decoder library must not depend on the oracle
-    data = open(mapdec.LIB_PATH, "rb").read()
-    assert b"orc_decode" not in data and b"liboracle" not in data
+    """The decoder library neither depends on the oracle's library nor imports or
+    exports any oracle symbol: its dynamic section (NEEDED entries) and its
+    dynamic symbol table, defined and undefined, are checked."""
+    import shutil
+    import subprocess
+    readelf, nm = shutil.which("readelf"), shutil.which("nm")
+    if not readelf or not nm:
+        pytest.skip("binutils not available")
+    dyn = subprocess.run([readelf, "-d", mapdec.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    needed = [ln for ln in dyn.splitlines() if "(NEEDED)" in ln]
+    assert needed, "no NEEDED entries read"
+    assert not any("oracle" in ln for ln in needed), needed
+    syms = subprocess.run([nm, "-D", mapdec.LIB_PATH], capture_output=True, text=True,
+                          check=True).stdout.split("\n")
+    names = [ln.split()[-1] for ln in syms if ln.strip()]
+    assert "mapdec_decode" in names
+    assert not [s for s in names if s.startswith("orc_")], "oracle symbol in the library"
 
 
 @pytest.mark.skipif(os.environ.get("CUDA_VISIBLE_DEVICES", None) is None and

@@ -4,7 +4,8 @@ one frame at a time.
 
   mixed-4096 : all 4096 frames decoded; every frame's status checked; a
                sample of frames across the (q, n) classes compared with the
-               oracle element by element.
+               oracle element by element, and the costliest frames of every
+               class against committed oracle references.
   grad-256   : 256 frames N=2000, q=32, n=8 in gradient mode; frames 0-3
                against central finite differences (h = 1e-6) of the FP64
                oracle and against its dual-number gradient.
@@ -18,7 +19,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import check_app, check_grad, check_ll
+from parity import check_app, check_grad, check_grad_priors, check_ll
 from paper_1802_08483_gb300 import mapdec, synth
 
 pytestmark = pytest.mark.gpu
@@ -81,6 +82,20 @@ def test_mixed_4096_full_batch():
         check_ll(ll[k], ll_ref, what=f"frame {k}")
         worst = max(worst, rel)
     print(f"mixed-4096: {len(sample)} frames checked, worst APP rel {worst:.2e}")
+    # the costliest frames of every (q, n) class (N near 4000, the widest drift
+    # limits), which dominate the timed step, against committed FP64 oracle
+    # references (tests/golden/make_mixed_golden.py: every 16th symbol's APPs
+    # and log P; kappa = 1.5 for two of them)
+    import os
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "mixed4096_heavy.npz"))
+    stride = int(gold["stride"])
+    assert {(frames[int(k)].q, frames[int(k)].n) for k in gold["frames"]} == set(synth.QN_CHOICES)
+    for k in [int(x) for x in gold["frames"]]:
+        rel, ab = check_app(apps[k][::stride], gold[f"app{k}"], what=f"heavy frame {k}")
+        llr = check_ll(ll[k], float(gold[f"ll{k}"]), what=f"heavy frame {k}")
+        fr = frames[k]
+        print(f"mixed-4096 heavy frame {k} (q={fr.q} n={fr.n} N={fr.N} xmax={fr.xmax}): "
+              f"APP rel {rel:.2e} abs {ab:.2e}, log P rel {llr:.2e}")
     b.close()
 
 
@@ -106,10 +121,10 @@ def test_grad_256_fd_on_first_frames():
             ld = oracle.loglik(fr.codebook, fr.N, *dn, fr.I, fr.xmax, fr.rx, priors=pri)
             fd = (lu - ld) / (2 * h)
             # central-difference rounding noise ~ N eps |log c| / h (a few 1e-6 here)
-            assert abs(dchan_ref[c] - fd) <= 1e-4 * max(1.0, abs(fd)), (k, c, dchan_ref[c], fd)
-            rel = abs(dchan[k, c] - fd) / max(abs(fd), 1.0)
-            assert rel <= 1e-4, (k, c, dchan[k, c], fd, rel)
-        check_grad(dpris[k], dpri_ref, what=f"frame {k} priors")
+            check_grad([dchan_ref[c]], [fd], what=f"oracle frame {k} d/dchan[{c}] vs FD")
+            check_grad([dchan[k, c]], [fd], what=f"frame {k} d/dchan[{c}] vs FD")
+        check_grad(dchan[k], dchan_ref, what=f"frame {k} channel")
+        check_grad_priors(dpris[k], dpri_ref, pri, what=f"frame {k} priors")
     b.close()
 
 
