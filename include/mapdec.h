@@ -322,6 +322,12 @@ typedef struct {
                             forward and APP producers (decode only; about
                             (rho+1) * roundup4(q) * (n(I+1)+1) * 4 bytes per frame);
                             0 or -1: recompute them */
+    int tensor_cores;    /* 0 or 1: producers on the tensor cores where the class
+                            supports them (see mapdec_batch_tc_frames); 2: FP32
+                            CUDA-core producers */
+    int chain_threads;   /* block size of the recursion kernel: 128, 256 or 512
+                            (0 = 256); the batch takes the value of its last frame
+                            whose class sets it */
 } mapdec_tune_t;
 
 /* Set (t != NULL) or remove (t == NULL) the entry of class (q, n, I). */
@@ -333,6 +339,17 @@ int mapdec_tune_clear(void);
 
 /* Number of waves the batch's frames were split into (scratch budget). */
 int mapdec_batch_num_waves(mapdec_batch_t *b);
+
+/*
+ * Number of the batch's frames whose contractions run on the tensor cores
+ * (tcgen05, bf16 operands split into high and low parts, FP32 accumulation;
+ * an implementation choice, not in the paper).  The planner picks them for
+ * classes with q a multiple of 16 up to 64 and n >= 4 (the other frames use the
+ * FP32 CUDA-core producers); the environment variable MAPDEC_TC=0, read when a
+ * batch is created, keeps every frame on the CUDA-core producers.  -1 for a
+ * NULL batch.
+ */
+int mapdec_batch_tc_frames(mapdec_batch_t *b);
 
 /*
  * Measured FP32 FMA throughput of the current device in TFLOP/s (2 flops per

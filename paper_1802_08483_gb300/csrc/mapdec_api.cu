@@ -16,6 +16,7 @@
 #include <mutex>
 #include <set>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mapdec.h"
@@ -31,10 +32,24 @@ namespace {
 struct CudaErr {
     cudaError_t e;
 };
-#define CK(x)                                   \
-    do {                                        \
-        cudaError_t _e = (x);                   \
-        if (_e != cudaSuccess) throw CudaErr{_e}; \
+// MAPDEC_VERBOSE=1 (read once) names the failing CUDA call on stderr; the
+// caller always gets the MAPDEC_* status.
+bool verbose() {
+    static const bool v = [] {
+        const char *e = std::getenv("MAPDEC_VERBOSE");
+        return e && std::atoi(e) != 0;
+    }();
+    return v;
+}
+#define CK(x)                                                                            \
+    do {                                                                                 \
+        cudaError_t _e = (x);                                                            \
+        if (_e != cudaSuccess) {                                                         \
+            if (verbose())                                                               \
+                std::fprintf(stderr, "libmapdec: %s (%s:%d): %s\n", cudaGetErrorName(_e), \
+                             __FILE__, __LINE__, #x);                                    \
+            throw CudaErr{_e};                                                           \
+        }                                                                                \
     } while (0)
 
 int map_cuda(cudaError_t e) {
@@ -123,6 +138,8 @@ struct FrameHost {
     double cost = 0.0;
     int segK = 0, nseg = 1; // segmented mode: symbols per segment, segments
     bool store = false;     // keep the receiver metrics in HBM for the APP producer
+    bool tc = false;        // forward producer on the tensor cores
+    bool tcb = false;       // APP producer on the tensor cores
 };
 
 // Stored receiver metrics of a frame: T tiles of P*MN rows x roundup4(q) floats.
@@ -206,8 +223,8 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     for (int c : cand) {
         if (pass == 0 && c != want) continue;
         FrameDev t = f;
-        t.P = c;
-        t.S = symbols_span(c);
+        t.P = t.Pf = c;
+        t.S = t.Sf = symbols_span(c);
         t.nsub = std::max(1, 256 / c);
         t.S2 = symbols_span((long long)c * t.nsub);
         if (fwd_smem_bytes(t) > kFwdSmemBudget) continue;
@@ -241,6 +258,9 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     }
     f.T = (int)((f.rho + 1 + P - 1) / P);
     f.T2 = (f.T + f.nsub - 1) / f.nsub;
+    f.Pf = f.P;
+    f.Sf = f.S;
+    f.Tf = f.T;
     // chain chunk: all states at once if it fits, else the largest power of two;
     // as many stages in flight as the budget allows (at least two)
     size_t cbud = kChainSmemBudget;
@@ -281,6 +301,54 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     CD = std::max(CD, (f.M + 63) / 64);
     f.chainCD = CD;
     f.chainStages = stages;
+}
+
+// Forward tile of the tensor-core producer: the most positions whose
+// (position, length) rows fit two 128-row MMA tiles, with at most 256 symbols
+// per tile (the MMA's N) and the shared memory within the two-CTA budget.
+// Sets Pf, Sf, Tf; false if no tile fits (the CUDA-core producer is used).
+bool plan_fwd_tc(FrameDev &f) {
+    if (!fwd_tc_supported(f.q, f.n, f.I)) return false;
+    for (int P = 32; P >= 1; --P) {
+        if (P * f.MN > 256) continue;
+        FrameDev t = f;
+        t.Pf = P;
+        t.Sf = (int)std::min<long long>(((long long)P - 1 + 2LL * f.xmax) / f.n + 2, f.N);
+        if (((t.Sf + 15) & ~15) > 256) continue;
+        if (fwd_tc_smem_bytes(t) > kFwdSmemBudget) continue;
+        f.Pf = t.Pf;
+        f.Sf = t.Sf;
+        f.Tf = (int)((f.rho + 1 + P - 1) / P);
+        return true;
+    }
+    return false;
+}
+
+// APP-producer tiling of the tensor-core kernel (decode mode): one lattice per
+// thread per sub-tile (P = 256 / q positions), as many sub-tiles per super-tile
+// (up to 256 positions) as keep its symbols within the 128 accumulator rows,
+// shared memory within the two-CTA budget.  Sets P, S, nsub, S2, T, T2; false
+// if no tiling fits (the CUDA-core producer and the planner's tiling stay).
+bool plan_bwd_tc(FrameDev &f) {
+    if (!fwd_tc_supported(f.q, f.n, f.I)) return false;
+    auto span = [&](long long Ppos) -> int {
+        return (int)std::min<long long>((Ppos - 1 + 2LL * f.xmax) / f.n + 2, f.N);
+    };
+    for (int P = 256 / f.q; P >= 1; --P) {
+        FrameDev t = f;
+        t.P = P;
+        t.S = span(P);
+        int nsub = std::max(1, 256 / P);
+        while (nsub > 1 && span((long long)P * nsub) > 128) --nsub;
+        t.nsub = nsub;
+        t.S2 = span((long long)P * nsub);
+        if (t.S2 > 128 || bwd_tc_smem_bytes(t) > kBwdSmemBudget) continue;
+        t.T = (int)((t.rho + 1 + P - 1) / P);
+        t.T2 = (t.T + t.nsub - 1) / t.nsub;
+        f = t;
+        return true;
+    }
+    return false;
 }
 
 size_t frame_scratch_floats(const FrameDev &f, bool grad) {
@@ -324,8 +392,16 @@ double frame_cost(const FrameDev &f) {
     return 2.0 * lat + 4.0 * band * f.q + 4.0 * band;
 }
 
+// Producer launches are grouped by (n, I) (the compiled lattice) and by the
+// forward producer's kind.
+using ClassKey = std::tuple<int, int, int>;  // n, I, tensor-core bits (kTcFwd | kTcBwd)
+
+constexpr int kTcFwd = 1, kTcBwd = 2;  // ClassKey / FrameHost tensor-core bits
+
 struct ClassLaunch {
     int n, I;
+    bool tc = false;   // forward producer on the tensor cores (producers_tc.cuh)
+    bool tcb = false;  // APP producer on the tensor cores
     Work *d_fwd = nullptr; int nfwd = 0; size_t smem_fwd = 0;
     Work *d_bwd = nullptr; int nbwd = 0; size_t smem_bwd = 0;
 };
@@ -441,7 +517,7 @@ namespace {
 // buffer bases shifted so that absolute symbol, row and super-tile indices land
 // in the frame's one-segment buffers) and the work lists of that segment.
 void build_segments(mapdec_batch *b, Wave &w, const std::vector<FrameDev> &devs,
-                    const std::map<std::pair<int, int>, std::vector<int>> &byclass) {
+                    const std::map<ClassKey, std::vector<int>> &byclass) {
     const int nw = w.f1 - w.f0;
     int Smax = 0;
     for (int k = 0; k < nw; ++k) Smax = std::max(Smax, b->fr[w.f0 + k].nseg);
@@ -496,8 +572,10 @@ void build_segments(mapdec_batch *b, Wave &w, const std::vector<FrameDev> &devs,
         upload(fin, sl.d_fin, sl.nfin);
         for (const auto &kv : byclass) {
             ClassLaunch c;
-            c.n = kv.first.first;
-            c.I = kv.first.second;
+            c.n = std::get<0>(kv.first);
+            c.I = std::get<1>(kv.first);
+            c.tc = (std::get<2>(kv.first) & kTcFwd) != 0;
+            c.tcb = (std::get<2>(kv.first) & kTcBwd) != 0;
             std::vector<Work> fw, bwk;
             for (int k : kv.second) {
                 const FrameHost &h = b->fr[w.f0 + k];
@@ -506,10 +584,10 @@ void build_segments(mapdec_batch *b, Wave &w, const std::vector<FrameDev> &devs,
                 const long long P2 = (long long)f.P * f.nsub;
                 const long long plo = std::max(0LL, (long long)f.n * f.seg_i0 - f.xmax);
                 const long long phi = std::min(f.rho, (long long)f.n * (f.seg_i1 - 1) + f.xmax);
-                for (long long t = plo / f.P; t <= phi / f.P; ++t) fw.push_back({k, (int)t});
+                for (long long t = plo / f.Pf; t <= phi / f.Pf; ++t) fw.push_back({k, (int)t});
                 for (long long t = plo / P2; t <= phi / P2; ++t) bwk.push_back({k, (int)t});
-                c.smem_fwd = std::max(c.smem_fwd, fwd_smem_bytes(f));
-                c.smem_bwd = std::max(c.smem_bwd, bwd_smem_bytes(f, b->grad));
+                c.smem_fwd = std::max(c.smem_fwd, c.tc ? fwd_tc_smem_bytes(f) : fwd_smem_bytes(f));
+                c.smem_bwd = std::max(c.smem_bwd, c.tcb ? bwd_tc_smem_bytes(f) : bwd_smem_bytes(f, b->grad));
             }
             upload(fw, c.d_fwd, c.nfwd);
             upload(bwk, c.d_bwd, c.nbwd);
@@ -543,6 +621,21 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         h.store = tuned && tu.store_metric == 1;
         if (const char *e = std::getenv("MAPDEC_STORE_R")) h.store = std::atoi(e) == 1;  // testing
         if (plain || b->grad || (flags & MAPDEC_BATCH_SEGMENTED)) h.store = false;
+        // tensor-core producers where the class supports it (default) in decode
+        // mode.  Gradient batches keep the FP32 contractions: d logP / d(Pi, Pd,
+        // Ps) is a sum of per-bit terms that nearly cancel, and the split-bf16 W
+        // (about 2^-16 per product) leaves it 3e-4 off relative on small
+        // gradients, where the FP32 W meets 1e-4.  MAPDEC_TC=0 keeps every frame
+        // on the CUDA-core producers (A/B tests).
+        bool tc_on = !(tuned && tu.tensor_cores == 2);
+        if (const char *e = std::getenv("MAPDEC_TC")) tc_on = std::atoi(e) != 0;
+        if (tuned && (tu.chain_threads == 128 || tu.chain_threads == 256 ||
+                      tu.chain_threads == 512))
+            b->chain_threads = tu.chain_threads;
+        h.tc = tc_on && !h.store && !b->grad && plan_fwd_tc(h.dev);
+        bool tcb_on = tc_on;
+        if (const char *e = std::getenv("MAPDEC_TC_BWD")) tcb_on = tcb_on && std::atoi(e) != 0;
+        h.tcb = tcb_on && h.tc && !b->grad && plan_bwd_tc(h.dev);
         if (flags & MAPDEC_BATCH_SEGMENTED) {
             int K = (int)std::ceil(std::sqrt((double)h.d.N));
             if (const char *e = std::getenv("MAPDEC_SEG_K")) {  // tuning / testing override
@@ -621,14 +714,14 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
     // per-wave descriptors and work tables
     const bool segmented = (flags & MAPDEC_BATCH_SEGMENTED) != 0;
     b->segmented = segmented;
-    if (const char *e = std::getenv("MAPDEC_CHAIN_THREADS")) b->chain_threads = std::atoi(e);  // tuning
+    if (const char *e = std::getenv("MAPDEC_CHAIN_THREADS")) b->chain_threads = std::atoi(e);  // A/B override
     for (size_t wi = 0; wi < b->waves.size(); ++wi) {
         Wave &w = b->waves[wi];
         size_t off = (wi % b->regions) * b->region_floats;
         std::vector<FrameDev> devs;
         std::vector<const uint8_t *> rxp;
         std::vector<uint32_t *> rxwp;
-        std::map<std::pair<int, int>, std::vector<int>> byclass;
+        std::map<ClassKey, std::vector<int>> byclass;
         for (int i = w.f0; i < w.f1; ++i) {
             FrameHost &h = b->fr[i];
             FrameDev f = h.dev;
@@ -688,7 +781,8 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             rxp.push_back(b->d_rx + h.rx_off);
             rxwp.push_back(b->d_rxw + h.rxw_off);
             w.max_words = std::max<long long>(w.max_words, (h.d.rx_len + 31) / 32 + 3);
-            byclass[{h.d.n, h.d.I}].push_back(i - w.f0);
+            byclass[ClassKey{h.d.n, h.d.I, (h.tc ? kTcFwd : 0) | (h.tcb ? kTcBwd : 0)}].push_back(
+                i - w.f0);
         }
         const int nw = w.f1 - w.f0;
         w.d_frames = (FrameDev *)b->dalloc(sizeof(FrameDev) * nw);
@@ -725,15 +819,17 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         CK(cudaMemcpy(w.d_chain, chain.data(), sizeof(Work) * chain.size(), cudaMemcpyHostToDevice));
         for (auto &kv : byclass) {
             ClassLaunch c;
-            c.n = kv.first.first;
-            c.I = kv.first.second;
+            c.n = std::get<0>(kv.first);
+            c.I = std::get<1>(kv.first);
+            c.tc = (std::get<2>(kv.first) & kTcFwd) != 0;
+            c.tcb = (std::get<2>(kv.first) & kTcBwd) != 0;
             std::vector<Work> fw, bw;
             for (int k : kv.second) {
                 const FrameDev &f = devs[k];
-                for (int t = 0; t < f.T; ++t) fw.push_back({k, t});
+                for (int t = 0; t < f.Tf; ++t) fw.push_back({k, t});
                 for (int t = 0; t < f.T2; ++t) bw.push_back({k, t});
-                c.smem_fwd = std::max(c.smem_fwd, fwd_smem_bytes(f));
-                c.smem_bwd = std::max(c.smem_bwd, bwd_smem_bytes(f, b->grad));
+                c.smem_fwd = std::max(c.smem_fwd, c.tc ? fwd_tc_smem_bytes(f) : fwd_smem_bytes(f));
+                c.smem_bwd = std::max(c.smem_bwd, c.tcb ? bwd_tc_smem_bytes(f) : bwd_smem_bytes(f, b->grad));
             }
             c.nfwd = (int)fw.size();
             c.nbwd = (int)bw.size();
@@ -791,7 +887,8 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         Wave &wv = b->waves[w];
         mark(w, 1, 0, st);
         for (auto &c : wv.cls) {
-            CK(launch_fwd(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
+            CK(c.tc ? launch_fwd_tc(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st)
+                    : launch_fwd(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
             ++launches;
         }
         mark(w, 1, 1, st);
@@ -810,7 +907,8 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         CK(cudaStreamWaitEvent(st, b->dep[2 * w + 1], 0));
         mark(w, 3, 0, st);
         for (auto &c : wv.cls) {
-            CK(launch_bwd(c.n, c.I, grad, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
+            CK(c.tcb ? launch_bwd_tc(c.n, c.I, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st)
+                     : launch_bwd(c.n, c.I, grad, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
             ++launches;
         }
         mark(w, 3, 1, st);
@@ -868,7 +966,8 @@ int64_t enqueue_run_seg(mapdec_batch *b, bool grad, cudaStream_t st) {
         auto fwd = [&](SegLaunch &sl) {
             for (auto &c : sl.cls) {
                 if (c.nfwd == 0) continue;
-                CK(launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
+                CK(c.tc ? launch_fwd_tc(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st)
+                        : launch_fwd(c.n, c.I, sl.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
                 ++launches;
             }
         };
@@ -907,7 +1006,8 @@ int64_t enqueue_run_seg(mapdec_batch *b, bool grad, cudaStream_t st) {
             CK(cudaStreamWaitEvent(st, sl.ev_chain2, 0));
             for (auto &c : sl.cls) {
                 if (c.nbwd == 0) continue;
-                CK(launch_bwd(c.n, c.I, grad, sl.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
+                CK(c.tcb ? launch_bwd_tc(c.n, c.I, sl.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st)
+                         : launch_bwd(c.n, c.I, grad, sl.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
                 ++launches;
             }
             CK(launch_finalize(sl.d_frames, sl.d_fin, sl.nfin, nw, grad ? 1 : 0, st,
@@ -1277,6 +1377,13 @@ int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms) {
 
 int mapdec_batch_num_waves(mapdec_batch_t *b) { return b ? (int)b->waves.size() : -1; }
 
+int mapdec_batch_tc_frames(mapdec_batch_t *b) {
+    if (!b) return -1;
+    int c = 0;
+    for (const auto &h : b->fr) c += h.tc ? 1 : 0;
+    return c;
+}
+
 int mapdec_tune_set(int q, int n, int I, const mapdec_tune_t *t) {
     if (q < 2 || n < 1 || I < 1) return MAPDEC_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1361,11 +1468,12 @@ void retarget_single(mapdec_batch *b, int64_t rho, bool ext) {
     f.rho = rho;
     f.T = (int)((rho + 1 + f.P - 1) / f.P);
     f.T2 = (f.T + f.nsub - 1) / f.nsub;
+    f.Tf = (int)((rho + 1 + f.Pf - 1) / f.Pf);
     f.ext = ext ? b->d_ext : nullptr;
     b->rx_total = rho;
     Wave &w = b->waves[0];
     for (auto &c : w.cls) {
-        c.nfwd = f.T;
+        c.nfwd = f.Tf;
         c.nbwd = f.T2;
     }
     CK(cudaMemcpyAsync(w.d_frames, &f, sizeof(FrameDev), cudaMemcpyHostToDevice, b->stream));
@@ -1504,7 +1612,7 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
         return o;
     };
     const size_t o_frame = take(sizeof(FrameDev));
-    const size_t o_fwd = take(sizeof(Work) * (size_t)f.T);
+    const size_t o_fwd = take(sizeof(Work) * (size_t)f.Tf);
     const size_t o_bwd = take(sizeof(Work) * (size_t)f.T2);
     const size_t o_chain = take(sizeof(Work) * 2);
     const int nfin = finalize_chunks(d.N);
@@ -1550,7 +1658,7 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     Work *wf = (Work *)(A + o_fwd), *wb = (Work *)(A + o_bwd), *wc = (Work *)(A + o_chain);
     Work *wfin = (Work *)(A + o_fin);
     const long long nuni = priors_dev ? 0 : (long long)d.N * d.q;
-    k_static_setup<<<64, 256, 0, s>>>(f, fdev, wf, f.T, wb, f.T2, wc, wfin, nfin,
+    k_static_setup<<<64, 256, 0, s>>>(f, fdev, wf, f.Tf, wb, f.T2, wc, wfin, nfin,
                                       (const uint8_t **)(A + o_rxp), (uint32_t **)(A + o_rxwp),
                                       rx_dev, (uint32_t *)(A + o_rxw), (uint32_t *)(A + o_cw), cb,
                                       d.q, (float *)(A + o_pri), nuni, 1.0f / (float)d.q,
@@ -1559,7 +1667,7 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     if (e == cudaSuccess)
         e = launch_pack(fdev, (const uint8_t *const *)(A + o_rxp), (uint32_t *const *)(A + o_rxwp), 1,
                         nwords, s);
-    if (e == cudaSuccess) e = launch_fwd(d.n, d.I, fdev, wf, f.T, fwd_smem_bytes(f), s);
+    if (e == cudaSuccess) e = launch_fwd(d.n, d.I, fdev, wf, f.Tf, fwd_smem_bytes(f), s);
     if (e == cudaSuccess) e = launch_chain(fdev, wc, 2, chain_smem_bytes(f), 0, s);
     if (e == cudaSuccess) e = launch_bwd(d.n, d.I, false, fdev, wb, f.T2, bwd_smem_bytes(f, false), s);
     if (e == cudaSuccess) e = launch_finalize(fdev, wfin, nfin, 1, 0, s);

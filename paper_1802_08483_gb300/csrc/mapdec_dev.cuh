@@ -46,9 +46,13 @@ struct FrameDev {
     int Mp;       // M rounded up to a multiple of 4 (row stride of alpha/beta)
     int MN;       // n(I+1) + 1 received lengths per symbol
     int MNS;      // row stride of W (odd, >= MN: bank-conflict-free smem rows)
-    int P;        // received positions per producer sub-tile
+    int P;        // received positions per APP-producer sub-tile
     int S;        // max symbols touched by one sub-tile
-    int T;        // forward tiles in this frame: ceil((rho+1)/P)
+    int T;        // sub-tiles in this frame: ceil((rho+1)/P)
+    int Pf;       // received positions per forward-producer tile (P unless the
+                  // tensor-core forward producer picked its own)
+    int Sf;       // max symbols touched by one forward tile
+    int Tf;       // forward tiles: ceil((rho+1)/Pf)
     int nsub;     // sub-tiles per backward super-tile
     int S2;       // max symbols touched by one super-tile (rows of Lp per super-tile)
     int T2;       // backward super-tiles: ceil(T / nsub)
@@ -129,10 +133,10 @@ __host__ __device__ inline void range_symbols(const FrameDev &f, long long p0, l
     ilo = (int)lo;
     ihi = (int)hi;
 }
-// Forward tile t covers positions [t P, t P + P - 1].
+// Forward tile t covers positions [t Pf, t Pf + Pf - 1].
 __host__ __device__ inline void tile_symbols(const FrameDev &f, int tile, int &ilo, int &ihi) {
-    const long long p0 = (long long)tile * f.P;
-    range_symbols(f, p0, p0 + f.P - 1, ilo, ihi);
+    const long long p0 = (long long)tile * f.Pf;
+    range_symbols(f, p0, p0 + f.Pf - 1, ilo, ihi);
 }
 // Backward super-tile t covers positions [t P nsub, (t+1) P nsub - 1].
 __host__ __device__ inline void super_symbols(const FrameDev &f, int tile, int &ilo, int &ihi) {

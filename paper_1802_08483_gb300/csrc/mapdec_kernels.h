@@ -10,20 +10,27 @@
 
 namespace mdk {
 
-// Raise a kernel's dynamic shared-memory opt-in to `bytes` on the current
-// device, once per device: the attribute is held per device, so a process that
-// launches on several GPUs sets it on each.  `done` has one bit per device
-// (devices 0..63; beyond that the attribute is set on every call).  Safe to
-// call from several threads: concurrent first calls may both set the same
-// value, which is harmless.
+// Raise a kernel's dynamic shared-memory opt-in to the device's per-block
+// maximum less the kernel's static shared memory, once per device: the
+// attribute is held per device, so a process that launches on several GPUs
+// sets it on each.  `done` has one bit per device (devices 0..63; beyond that
+// the attribute is set on every call).  Safe to call from several threads:
+// concurrent first calls may both set the same value, which is harmless.
 template <typename Kern>
-cudaError_t smem_optin_once(Kern kern, int bytes, std::atomic<uint64_t> &done) {
+cudaError_t smem_optin_once(Kern kern, std::atomic<uint64_t> &done) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
     if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
     return e;
 }
@@ -38,6 +45,18 @@ cudaError_t launch_rmetric(int n, int I, const FrameDev *frame, long long nthrea
                            cudaStream_t st);
 bool specialised(int n, int I);
 size_t fwd_smem_bytes(const FrameDev &f);
+// Tensor-core forward producer (producers_tc.cuh): which frames it serves,
+// its shared memory, and its launch.
+bool fwd_tc_supported(int q, int n, int I);
+size_t fwd_tc_smem_bytes(const FrameDev &f);
+cudaError_t launch_fwd_tc(int n, int I, const FrameDev *frames, const Work *work, int nwork,
+                          size_t smem, cudaStream_t st);
+// Tensor-core APP producer (decode mode): same class rule, S2 <= 128.
+size_t bwd_tc_smem_bytes(const FrameDev &f);
+cudaError_t launch_bwd_tc(int n, int I, const FrameDev *frames, const Work *work, int nwork,
+                          size_t smem, cudaStream_t st);
+constexpr size_t kTcMinSmem = 80 * 1024;  // caps the tensor-core producers at 2 CTAs per SM
+constexpr int kTcChunkCols = 80;          // A-operand columns per chunk of the APP producer
 size_t bwd_smem_bytes(const FrameDev &f, bool grad);
 
 cudaError_t launch_pack(const FrameDev *frames, const uint8_t *const *rx_bytes,
@@ -63,7 +82,11 @@ int finalize_chunks(int N);  // work items (frame, chunk) per frame
     cudaError_t launch_bwd_I##IB##_plain(int n, const FrameDev *frames, const Work *work,    \
                                          int nwork, size_t smem, cudaStream_t st);            \
     cudaError_t launch_bwd_I##IB##_grad(int n, const FrameDev *frames, const Work *work,     \
-                                        int nwork, size_t smem, cudaStream_t st);
+                                        int nwork, size_t smem, cudaStream_t st);            \
+    cudaError_t launch_fwd_tc_I##IB(int n, const FrameDev *frames, const Work *work,         \
+                                    int nwork, size_t smem, cudaStream_t st);                \
+    cudaError_t launch_bwd_tc_I##IB(int n, const FrameDev *frames, const Work *work,         \
+                                    int nwork, size_t smem, cudaStream_t st);
 MAPDEC_DECLARE_I(1)
 MAPDEC_DECLARE_I(2)
 MAPDEC_DECLARE_I(3)

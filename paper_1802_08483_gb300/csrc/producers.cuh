@@ -69,7 +69,7 @@ __device__ __forceinline__ void fwd_body(const FrameDev *__restrict__ frames,
     const FrameDev &f = frames[wk.frame];
     const int n = (NB == 0) ? f.n : NB;
     const int MN = (NB == 0) ? f.MN : NB * (IB + 1) + 1;
-    const int q = f.q, P = f.P, M = f.M, xmax = f.xmax;
+    const int q = f.q, P = f.Pf, M = f.M, xmax = f.xmax;
     const long long rho = f.rho;
     const long long p0 = (long long)wk.tile * P;
     int ilo, ihi;
@@ -189,6 +189,115 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_occ2(const FrameDev *__rest
 }
 
 // ---------------------------------------------------------------------------
+// alpha and beta windows of an APP-producer sub-tile (positions p0 .. p0+P-1,
+// symbols ilo .. ilo+S-1, row stride S4 >= S), with the exact factor that
+// undoes the chains' tilts (k_chain):
+//   sigma ~ alpha^_i(m') beta^_{i+1}(m) 2^{(theta'_{i+1} - theta_i)(m' - mean_i)}
+//           2^{(theta'_{i+1} - 1) j} prior R~
+// up to a constant per symbol.  The per-j factor 2^{phi j}, phi =
+// theta'_{i+1} - 1, splits exactly as 2^{phi (pl + j)} 2^{-phi pl}: folded
+// into the beta window (index pl + j) and the alpha window (index pl).
+// With m' = p0 + pl - n i the alpha-side exponent is e0_i + g_i pl,
+// e0_i = (theta'_{i+1} - theta_i)(p0 - n i - mean_i) (split into integer and
+// fraction), g_i = theta'_{i+1} - theta_i - phi; the factor is applied as
+// alpha 2^frac scaled by 2^int (exact), clamped below overflow.  The tilts
+// and means are FP32 values, so e0_i is formed exactly enough in FP32 pairs
+// (error-free sum and product): its integer part exactly, its fraction to a
+// few FP32 ulps.
+// Windows: Aw[pl][il] = alpha_i(state of p0 + pl), Bw[k][il] =
+// beta_{i+1}(state of p0 - n + k), k < BW = P + MN - 1, zero outside the
+// limits or past rho.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void window_constants(const FrameDev &f, long long p0, int n, int ilo,
+                                                 int S, int S4, int *symE, float *symF,
+                                                 float *symG, float *symPhi) {
+    for (int il = threadIdx.x; il < S4; il += blockDim.x) {
+        int ei = 0;
+        float ef = 0.f, g = 0.f, phi = 0.f;
+        if (il < S) {
+            const long long i = ilo + il;
+            const float tb = (float)f.thb[i + 1], tf = (float)f.thf[i];
+            const float mu = (float)f.mcf[i];
+            // dth = tb - tf and x = (p0 - n i) - mu as unevaluated sums hi + lo
+            float dh, dl, xh, xl;
+            two_sum(tb, -tf, dh, dl);
+            two_sum((float)(p0 - (long long)n * i), -mu, xh, xl);
+            // e0 = dth x = ph + pl + (dh xl + dl xh) (dl xl is far below FP32 ulp)
+            const float ph0 = dh * xh;
+            const float pl0 = fmaf(dh, xh, -ph0);
+            const float r = rintf(ph0);
+            ei = (int)fmaxf(-100000.f, fminf(100000.f, r));
+            ef = ((ph0 - r) + pl0) + fmaf(dh, xl, dl * xh);
+            phi = tb - 1.f;
+            g = (dh - phi) + dl;
+        }
+        symE[il] = ei;
+        symF[il] = ef;
+        symG[il] = g;
+        symPhi[il] = phi;
+    }
+}
+
+// Raw rows fetched row by row (coalesced) by 4-byte asynchronous copies; the
+// caller waits for them (cp_async_wait_all) and a CTA barrier before use.
+// One symbol per warp, positions across the lanes (no divisions).
+__device__ __forceinline__ void window_fetch(const FrameDev &f, long long p0, int n, int ilo,
+                                             int S, int S4, int P, int BW, float *Aw,
+                                             float *Bw) {
+    const int M = f.M, xmax = f.xmax;
+    const long long rho = f.rho;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
+    for (int il = warp; il < S4; il += NW) {
+        const long long i = ilo + il;
+        const long long sa = p0 - (long long)n * i + xmax;  // state of position p0
+        const float *arow = f.alpha + (size_t)i * f.Mp;
+        const float *brow = f.beta + (size_t)(i + 1) * f.Mp;
+        for (int pl = lane; pl < P; pl += 32) {
+            const long long s = sa + pl;
+            float *dst = Aw + pl * S4 + il;
+            if (il < S && s >= 0 && s < M && p0 + pl <= rho) cp_async4(dst, arow + s);
+            else *dst = 0.f;
+        }
+        for (int k = lane; k < BW; k += 32) {
+            const long long s = sa - n + k;
+            float *dst = Bw + k * S4 + il;
+            if (il < S && s >= 0 && s < M) cp_async4(dst, brow + s);
+            else *dst = 0.f;
+        }
+    }
+}
+
+// The tilt factors applied in place to the landed windows.
+__device__ __forceinline__ void window_tilt(int S, int S4, int P, int BW, float *Aw, float *Bw,
+                                            const int *symE, const float *symF,
+                                            const float *symG, const float *symPhi) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
+    for (int il = warp; il < S; il += NW) {
+        const float g = symG[il], fr = symF[il], phi = symPhi[il];
+        const int e0 = symE[il];
+        for (int pl = lane; pl < P; pl += 32) {
+            float *ap = Aw + pl * S4 + il;
+            const float a = *ap;
+            if (a > 0.f) {
+                const float e = fmaf(g, (float)pl, fr);
+                const float k = rintf(e);
+                const int ex = min(max(e0 + (int)k, -300), 300);
+                // 2^ex as two exact powers of two within the FP32 exponent range
+                const int e1 = min(max(ex, -126), 127);
+                const int e2 = min(max(ex - e1, -126), 127);
+                const float v = a * exp2f(e - k);
+                *ap = fminf(v * pow2i(e1) * pow2i(e2), 3.0e38f);
+            }
+        }
+        for (int k = lane; k < BW; k += 32) {
+            float *bp = Bw + k * S4 + il;
+            const float b = *bp;
+            if (b != 0.f) *bp = b * exp2f(phi * (float)k);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Backward producer (APP partial sums, optional tangents).  One CTA owns a
 // super-tile of nsub sub-tiles of P positions and accumulates, in shared
 // memory, for every symbol i it touches:
@@ -248,69 +357,11 @@ __global__ void __launch_bounds__(kThreads, (GRAD && (NB == 0 || NB > 10)) ? 1 :
         const int S4 = (S + 3) & ~3;
         const int off = ilo - ilo2;  // row of symbol ilo in the accumulators
 
-        // (B) alpha and beta windows of the sub-tile's symbols, with the exact
-        // factor that undoes the chains' tilts (k_chain):
-        //   sigma ~ alpha^_i(m') beta^_{i+1}(m) 2^{(theta'_{i+1} - theta_i)(m' - mean_i)}
-        //           2^{(theta'_{i+1} - 1) j} prior R~
-        // up to a constant per symbol.  The per-j factor 2^{phi j}, phi =
-        // theta'_{i+1} - 1, splits exactly as 2^{phi (pl + j)} 2^{-phi pl}: folded
-        // into the beta window (index pl + j) and the alpha window (index pl).
-        // With m' = p0 + pl - n i the alpha-side exponent is e0_i + g_i pl,
-        // e0_i = (theta'_{i+1} - theta_i)(p0 - n i - mean_i) (FP64, split into
-        // integer and fraction), g_i = theta'_{i+1} - theta_i - phi; the factor
-        // is applied as alpha 2^frac scaled by 2^int (exact), clamped below
-        // overflow.  The tilts and means are FP32 values, so e0_i is formed
-        // exactly enough in FP32 pairs (error-free sum and product): its integer
-        // part exactly, its fraction to a few FP32 ulps.  The raw rows are
-        // fetched here, row by row (coalesced), by asynchronous copies that
-        // land while the lattices below run.
-        for (int il = threadIdx.x; il < S4; il += blockDim.x) {
-            int ei = 0;
-            float ef = 0.f, g = 0.f, phi = 0.f;
-            if (il < S) {
-                const long long i = ilo + il;
-                const float tb = (float)f.thb[i + 1], tf = (float)f.thf[i];
-                const float mu = (float)f.mcf[i];
-                // dth = tb - tf and x = (p0 - n i) - mu as unevaluated sums hi + lo
-                float dh, dl, xh, xl;
-                two_sum(tb, -tf, dh, dl);
-                two_sum((float)(p0 - (long long)n * i), -mu, xh, xl);
-                // e0 = dth x = ph + pl + (dh xl + dl xh) (dl xl is far below FP32 ulp)
-                const float ph0 = dh * xh;
-                const float pl0 = fmaf(dh, xh, -ph0);
-                const float r = rintf(ph0);
-                ei = (int)fmaxf(-100000.f, fminf(100000.f, r));
-                ef = ((ph0 - r) + pl0) + fmaf(dh, xl, dl * xh);
-                phi = tb - 1.f;
-                g = (dh - phi) + dl;
-            }
-            symE[il] = ei;
-            symF[il] = ef;
-            symG[il] = g;
-            symPhi[il] = phi;
-        }
-        {
-            // one symbol per warp, positions across the lanes (no divisions)
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
-            for (int il = warp; il < S4; il += NW) {
-                const long long i = ilo + il;
-                const long long sa = p0 - (long long)n * i + xmax;  // state of position p0
-                const float *arow = f.alpha + (size_t)i * f.Mp;
-                const float *brow = f.beta + (size_t)(i + 1) * f.Mp;
-                for (int pl = lane; pl < P; pl += 32) {
-                    const long long s = sa + pl;
-                    float *dst = Aw + pl * S4 + il;
-                    if (il < S && s >= 0 && s < M && p0 + pl <= rho) cp_async4(dst, arow + s);
-                    else *dst = 0.f;
-                }
-                for (int k = lane; k < BW; k += 32) {
-                    const long long s = sa - n + k;
-                    float *dst = Bw + k * S4 + il;
-                    if (il < S && s >= 0 && s < M) cp_async4(dst, brow + s);
-                    else *dst = 0.f;
-                }
-            }
-        }
+        // (B) alpha and beta windows of the sub-tile's symbols (see
+        // window_constants / window_fetch); the raw rows land while the
+        // lattices below run.
+        window_constants(f, p0, n, ilo, S, S4, symE, symF, symG, symPhi);
+        window_fetch(f, p0, n, ilo, S, S4, P, BW, Aw, Bw);
 
         // (A) receiver metrics (and tangents); lanes cover consecutive D for one p.
         // Decode mode with stored metrics: copy the tile's block instead.
@@ -346,35 +397,10 @@ __global__ void __launch_bounds__(kThreads, (GRAD && (NB == 0 || NB > 10)) ? 1 :
             }
         }
         // (B) the windows' raw alpha/beta values have landed: apply the tilt
-        // factors in place (see above).
+        // factors in place.
         cp_async_wait_all();
         __syncthreads();
-        {
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
-            for (int il = warp; il < S; il += NW) {
-                const float g = symG[il], fr = symF[il], phi = symPhi[il];
-                const int e0 = symE[il];
-                for (int pl = lane; pl < P; pl += 32) {
-                    float *ap = Aw + pl * S4 + il;
-                    const float a = *ap;
-                    if (a > 0.f) {
-                        const float e = fmaf(g, (float)pl, fr);
-                        const float k = rintf(e);
-                        const int ex = min(max(e0 + (int)k, -300), 300);
-                        // 2^ex as two exact powers of two within the FP32 exponent range
-                        const int e1 = min(max(ex, -126), 127);
-                        const int e2 = min(max(ex - e1, -126), 127);
-                        const float v = a * exp2f(e - k);
-                        *ap = fminf(v * pow2i(e1) * pow2i(e2), 3.0e38f);
-                    }
-                }
-                for (int k = lane; k < BW; k += 32) {
-                    float *bp = Bw + k * S4 + il;
-                    const float b = *bp;
-                    if (b != 0.f) *bp = b * exp2f(phi * (float)k);
-                }
-            }
-        }
+        window_tilt(S, S4, P, BW, Aw, Bw, symE, symF, symG, symPhi);
         __syncthreads();
 
         // (C) register micro-tiles of 4 symbols x 4 columns.  With fewer

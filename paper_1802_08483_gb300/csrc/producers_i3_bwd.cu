@@ -13,4 +13,12 @@ cudaError_t launch_bwd_I3_plain(int n, const FrameDev *frames, const Work *work,
     }
 }
 
+cudaError_t launch_bwd_tc_I3(int n, const FrameDev *frames, const Work *work, int nwork,
+                             size_t smem, cudaStream_t st) {
+    switch (n) {
+        MAPDEC_FOR_N_TC(MAPDEC_CASE_BWDTC)
+        default: return cudaErrorNotSupported;
+    }
+}
+
 }  // namespace mdk

@@ -12,6 +12,14 @@ cudaError_t launch_fwd_I3(int n, const FrameDev *frames, const Work *work, int n
     }
 }
 
+cudaError_t launch_fwd_tc_I3(int n, const FrameDev *frames, const Work *work, int nwork,
+                             size_t smem, cudaStream_t st) {
+    switch (n) {
+        MAPDEC_FOR_N_TC(MAPDEC_CASE_FWDTC)
+        default: return cudaErrorNotSupported;
+    }
+}
+
 cudaError_t launch_rmetric_I3(int n, const FrameDev *frame, long long nthreads, cudaStream_t st) {
     switch (n) {
         MAPDEC_FOR_N(MAPDEC_CASE_RM)

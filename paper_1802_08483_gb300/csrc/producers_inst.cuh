@@ -3,10 +3,9 @@
 
 #include "mapdec_kernels.h"
 #include "producers.cuh"
+#include "producers_tc.cuh"
 
 namespace mdk {
-
-constexpr int kMaxDynSmem = 227 * 1024;  // producers use no static shared memory
 
 template <int NB, int IB>
 cudaError_t launch_fwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem, cudaStream_t st) {
@@ -16,7 +15,7 @@ cudaError_t launch_fwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem,
         else return k_fwd<NB, IB>;
     }();
     static std::atomic<uint64_t> attr{0};
-    cudaError_t e = smem_optin_once(kern, kMaxDynSmem, attr);
+    cudaError_t e = smem_optin_once(kern, attr);
     if (e != cudaSuccess) return e;
     if (nw <= 0) return cudaSuccess;
     kern<<<nw, kThreads, smem, st>>>(fr, w);
@@ -26,11 +25,43 @@ cudaError_t launch_fwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem,
 template <int NB, int IB, bool GRAD>
 cudaError_t launch_bwd_t(const FrameDev *fr, const Work *w, int nw, size_t smem, cudaStream_t st) {
     static std::atomic<uint64_t> attr{0};
-    cudaError_t e = smem_optin_once(k_bwd<NB, IB, GRAD>, kMaxDynSmem, attr);
+    cudaError_t e = smem_optin_once(k_bwd<NB, IB, GRAD>, attr);
     if (e != cudaSuccess) return e;
     if (nw <= 0) return cudaSuccess;
     k_bwd<NB, IB, GRAD><<<nw, kThreads, smem, st>>>(fr, w);
     return cudaGetLastError();
+}
+
+// Tensor-core forward producer (q a multiple of 16, n >= 4: see producers_tc.cuh).
+template <int NB, int IB>
+cudaError_t launch_fwd_tc_t(const FrameDev *fr, const Work *w, int nw, size_t smem,
+                            cudaStream_t st) {
+    if constexpr (NB >= 4) {
+        static std::atomic<uint64_t> attr{0};
+        cudaError_t e = smem_optin_once(k_fwd_tc<NB, IB>, attr);
+        if (e != cudaSuccess) return e;
+        if (nw <= 0) return cudaSuccess;
+        k_fwd_tc<NB, IB><<<nw, kThreads, smem, st>>>(fr, w);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+// Tensor-core APP producer, decode mode (producers_tc.cuh).
+template <int NB, int IB>
+cudaError_t launch_bwd_tc_t(const FrameDev *fr, const Work *w, int nw, size_t smem,
+                            cudaStream_t st) {
+    if constexpr (NB >= 4) {
+        static std::atomic<uint64_t> attr{0};
+        cudaError_t e = smem_optin_once(k_bwd_tc<NB, IB>, attr);
+        if (e != cudaSuccess) return e;
+        if (nw <= 0) return cudaSuccess;
+        k_bwd_tc<NB, IB><<<nw, kThreads, smem, st>>>(fr, w);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
 }
 
 template <int NB, int IB>
@@ -53,4 +84,7 @@ cudaError_t launch_rmetric_t(const FrameDev *fr, long long nthreads, cudaStream_
 #define MAPDEC_CASE_BWDX(NV) \
     case NV: return launch_bwd_t<NV, MAPDEC_IB, grad>(frames, work, nwork, smem, st);
 #define MAPDEC_CASE_RM(NV) case NV: return launch_rmetric_t<NV, MAPDEC_IB>(frame, nthreads, st);
+#define MAPDEC_CASE_FWDTC(NV) case NV: return launch_fwd_tc_t<NV, MAPDEC_IB>(frames, work, nwork, smem, st);
+#define MAPDEC_CASE_BWDTC(NV) case NV: return launch_bwd_tc_t<NV, MAPDEC_IB>(frames, work, nwork, smem, st);
+#define MAPDEC_FOR_N_TC(M) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)
 #define MAPDEC_FOR_N(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)

@@ -1,0 +1,390 @@
+// Tensor-core forward producer (tcgen05): the same work as k_fwd -- lattices
+// of a tile of Pf received positions (eqs. F / F_lastrow) and the prior-weighted
+// transition sums W_i(s', j) = sum_D prior_i(D) R[n i + s' - xmax][D][j] (eq.
+// gamma summed over D) -- with the contraction over D on the tensor cores.
+//
+// Per tile the contraction is the dense product
+//     C[k][il] = sum_D R[k][D] prior[ilo + il][D],   k = pl * MN + j,
+// M = the tile's Pf * MN (position, length) rows in 128-row tiles, N = the
+// tile's symbols (a multiple of 16, at most 256), K = q (a multiple of 16).
+// FP32 accuracy from bf16 operands: each operand x is split as x = hi + lo
+// (hi = bf16(x), lo = bf16(x - hi)) and C = Rhi Phi + Rhi Plo + Rlo Phi, three
+// MMAs accumulating in FP32 in tensor memory; the dropped Rlo Plo term and the
+// rounding of lo are about 2^-16 of each product.
+//
+// Shared memory: Rhi, Rlo [MT*128 rows][q] and Phi, Plo [NN rows][q], bf16,
+// K-major (layout in tcgen05.cuh).  Rows beyond the tile's data are never
+// written: they only feed output rows / columns that are not stored.
+// Tensor memory: 256 columns, two accumulators of 128 columns when NN <= 128
+// (the MMAs of M-tile t+1 overlap the epilogue of M-tile t), else one.
+// Every CTA that allocates tensor memory frees it before it exits; the waits
+// on MMA completion are bounded (ST_TIMEOUT).
+#pragma once
+
+#include "mapdec_kernels.h"
+#include "producers.cuh"
+#include "tcgen05.cuh"
+
+namespace mdk {
+
+constexpr int kTcCols = 256;  // tensor-memory columns per CTA (two CTAs per SM)
+constexpr uint32_t kTcWaitLimit = 1u << 26;
+
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
+    return mbar_wait(bar, parity, kTcWaitLimit);
+}
+
+template <int NB, int IB>
+__global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restrict__ frames,
+                                                        const Work *__restrict__ work) {
+    static_assert(NB > 0, "compile-time lattice only");
+    constexpr int n = NB;
+    constexpr int MN = NB * (IB + 1) + 1;
+    const Work wk = work[blockIdx.x];
+    const FrameDev &f = frames[wk.frame];
+    const int q = f.q, P = f.Pf, M = f.M, xmax = f.xmax;
+    const long long rho = f.rho;
+    const long long p0 = (long long)wk.tile * P;
+    int ilo, ihi;
+    tile_symbols(f, wk.tile, ilo, ihi);
+    const int S = ihi - ilo + 1;
+    if (S <= 0) return;  // uniform over the CTA, before any tensor memory is held
+    const int NC = P * MN;
+    const int MT = (NC + 127) >> 7;
+    const int NN = (S + 15) & ~15;
+    const int kc = q >> 3;
+    const int nbuf = NN <= 128 ? 2 : 1;
+
+    extern __shared__ __align__(128) unsigned char tsm[];
+    unsigned char *Rhi = tsm;
+    unsigned char *Rlo = Rhi + (size_t)MT * 128 * q * 2;
+    unsigned char *Phi = Rlo + (size_t)MT * 128 * q * 2;
+    unsigned char *Plo = Phi + (size_t)NN * q * 2;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(&s_tmem, kTcCols);
+    if (tid == 0) {
+        s_fail = 0;
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_mbar_init();
+    }
+
+    // (A) lattices: a warp covers 4 positions x 8 codewords (conflict-free
+    // stores: MN is odd, so the 4 rows land in distinct 16-byte row slots)
+    const int nblk = ((P + 3) >> 2) * (q >> 3);
+    for (int b = warp; b < nblk; b += kThreads / 32) {
+        const int pb = b / (q >> 3), db = b - pb * (q >> 3);
+        const int pl = pb * 4 + (lane >> 3), D = db * 8 + (lane & 7);
+        if (pl >= P) continue;
+        const long long p = p0 + pl;
+        float v[kMaxMN];
+        if (p <= rho) {
+            eval_metric<NB, IB, 0>(f, p, D, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < MN; ++j) v[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < MN; ++j) {
+            __nv_bfloat16 h, l;
+            tc::split_bf16(v[j], h, l);
+            const uint32_t o = tc::op_offset(pl * MN + j, D, kc);
+            *reinterpret_cast<__nv_bfloat16 *>(Rhi + o) = h;
+            *reinterpret_cast<__nv_bfloat16 *>(Rlo + o) = l;
+        }
+    }
+    // (B) priors of the touched symbols, rows il < S
+    for (int e = tid; e < S * q; e += kThreads) {
+        const int il = e / q, D = e - il * q;
+        __nv_bfloat16 h, l;
+        tc::split_bf16(__ldg(f.priors + (size_t)(ilo + il) * q + D), h, l);
+        const uint32_t o = tc::op_offset(il, D, kc);
+        *reinterpret_cast<__nv_bfloat16 *>(Phi + o) = h;
+        *reinterpret_cast<__nv_bfloat16 *>(Plo + o) = l;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = tc::idesc_bf16(128, NN);
+
+    // MMAs of M-tile t into accumulator t % nbuf (one thread)
+    auto issue = [&](int t) {
+        const uint32_t d = tmem + (uint32_t)((t % nbuf) * 128);
+        const uint32_t aoff = (uint32_t)t * 16u * (uint32_t)kc * 128u;  // 128 rows = 16 groups
+        const uint32_t ah = smem_u32(Rhi) + aoff, al = smem_u32(Rlo) + aoff;
+        const uint32_t bh = smem_u32(Phi), bl = smem_u32(Plo);
+        for (int k0 = 0; k0 < q; k0 += 16) {
+            const uint32_t ko = (uint32_t)(k0 >> 3) * 128u;
+            tc::mma_bf16(d, tc::smem_desc(ah + ko, kc), tc::smem_desc(bh + ko, kc), idesc,
+                         k0 > 0 ? 1u : 0u);
+            tc::mma_bf16(d, tc::smem_desc(ah + ko, kc), tc::smem_desc(bl + ko, kc), idesc, 1u);
+            tc::mma_bf16(d, tc::smem_desc(al + ko, kc), tc::smem_desc(bh + ko, kc), idesc, 1u);
+        }
+        tc::commit(&s_bar[t % nbuf]);
+    };
+    if (tid == 0)
+        for (int t = 0; t < nbuf && t < MT; ++t) issue(t);
+
+    // (C) epilogue per M-tile: TMEM lane = row k of the tile, 16 columns per load;
+    // the two warpgroups take alternate 16-column chunks.  For one symbol, 32
+    // consecutive rows k are 32 consecutive floats of W (MNS == MN).
+    const int lg = warp & 3, half = warp >> 2;
+    for (int t = 0; t < MT; ++t) {
+        const int buf = t % nbuf;
+        if (!tc_wait(&s_bar[buf], (uint32_t)((t / nbuf) & 1))) s_fail = ST_TIMEOUT;
+        tc::fence_after_sync();
+        const int k = t * 128 + lg * 32 + lane;
+        const int pl = k / MN, j = k - pl * MN;
+        const long long p = p0 + pl;
+        const bool rowok = k < NC && p <= rho && !s_fail;
+        const long long sbase = p - (long long)n * ilo + xmax;  // drift state for il = 0
+        const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * 128);
+        for (int c0 = half * 16; c0 < NN; c0 += 32) {
+            float v[16];
+            tc::ld16(ta + (uint32_t)c0, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int il = c0 + e;
+                const long long s = sbase - (long long)n * il;
+                if (rowok && il < S && s >= 0 && s < M)
+                    f.W[(size_t)(ilo + il) * f.wblk + s * f.MNS + j] = v[e];
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0 && t + nbuf < MT) {
+            tc::fence_after_sync();
+            issue(t + nbuf);
+        }
+    }
+    if (tid == 0 && s_fail) atomicMax(f.status, s_fail);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTcCols);
+}
+
+}  // namespace mdk
+
+namespace mdk {
+
+// ---------------------------------------------------------------------------
+// Tensor-core APP producer (decode mode).  Same work item and output as k_bwd
+// (a super-tile of nsub sub-tiles of P positions; Lp rows of the super-tile's
+// symbols), with the contraction of eqs. (L), (sigma) on the tensor cores:
+//     C[il2][D] += sum_k A[il2][k] R[D][k],   k = pl * MN + j,
+//     A[il2][k] = Aw[pl][il] Bw[pl + j][il]   (il = il2 - off: the sub-tile's
+//                                              symbols; other rows zero)
+// accumulated over every sub-tile in one TMEM accumulator of 128 lanes
+// (il2 < S2 <= 128) and q columns.  Both operands are split into bf16 hi + lo
+// and multiplied as hi*hi + hi*lo + lo*hi (FP32 accumulation).
+// Shared memory: Rhi, Rlo [q rows][Kp] (Kp = P*MN rounded up to 16, the pad
+// columns zero), Ahi, Alo [128 rows][kTcChunk] (A is built chunk by chunk of
+// kTcChunk columns and consumed by the MMAs before the next chunk), the
+// windows Aw, Bw (FP32) and the per-symbol tilt constants.
+// ---------------------------------------------------------------------------
+constexpr int kTcChunk = kTcChunkCols;  // A-operand columns per chunk (a multiple of 16)
+
+template <int NB, int IB>
+__global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restrict__ frames,
+                                                        const Work *__restrict__ work) {
+    static_assert(NB > 0, "compile-time lattice only");
+    constexpr int n = NB;
+    constexpr int MN = NB * (IB + 1) + 1;
+    const Work wk = work[blockIdx.x];
+    const FrameDev &f = frames[wk.frame];
+    const int q = f.q, P = f.P;
+    const long long rho = f.rho;
+    int ilo2, ihi2;
+    super_symbols(f, wk.tile, ilo2, ihi2);
+    const int S2 = ihi2 - ilo2 + 1;
+    if (S2 <= 0) return;  // uniform over the CTA, before any tensor memory is held
+    const int K = P * MN;
+    const int Kp = (K + 15) & ~15;
+    const int kcR = Kp >> 3;
+    constexpr int kcA = kTcChunk >> 3;
+    const int BW = P + MN - 1;
+    const int Smax4 = (f.S + 3) & ~3;
+    const uint32_t ncols = q <= 32 ? 32u : 64u;
+
+    extern __shared__ __align__(128) unsigned char tsm[];
+    unsigned char *Rhi = tsm;
+    unsigned char *Rlo = Rhi + (size_t)q * Kp * 2;
+    unsigned char *Ahi = Rlo + (size_t)q * Kp * 2;
+    unsigned char *Alo = Ahi + (size_t)128 * kTcChunk * 2;
+    float *Aw = reinterpret_cast<float *>(Alo + (size_t)128 * kTcChunk * 2);
+    float *Bw = Aw + (size_t)P * Smax4;
+    int *symE = reinterpret_cast<int *>(Bw + (size_t)BW * Smax4);
+    float *symF = reinterpret_cast<float *>(symE + Smax4);
+    float *symG = symF + Smax4;
+    float *symPhi = symG + Smax4;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(&s_tmem, ncols);
+    if (tid == 0) {
+        s_fail = 0;
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+    }
+    // pad columns K .. Kp-1 of R stay zero (the lattices write columns < K)
+    for (int e = tid; e < q * (Kp - K); e += kThreads) {
+        const int D = e / (Kp - K), k = K + e % (Kp - K);
+        const uint32_t o = tc::op_offset(D, k, kcR);
+        *reinterpret_cast<__nv_bfloat16 *>(Rhi + o) = __float2bfloat16_rn(0.f);
+        *reinterpret_cast<__nv_bfloat16 *>(Rlo + o) = __float2bfloat16_rn(0.f);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = tc::idesc_bf16(128, q);
+
+    uint32_t phase = 0;
+    bool pending = false;  // MMAs committed and not yet waited for
+    bool issued = false;   // the accumulator holds data
+    auto drain = [&]() {
+        if (pending) {
+            if (!tc_wait(&s_bar, phase)) s_fail = ST_TIMEOUT;
+            phase ^= 1u;
+            pending = false;
+            tc::fence_after_sync();
+        }
+    };
+
+    for (int sub = 0; sub < f.nsub; ++sub) {
+        const long long p0 = ((long long)wk.tile * f.nsub + sub) * P;
+        if (p0 > rho) break;
+        int ilo, ihi;
+        range_symbols(f, p0, p0 + P - 1, ilo, ihi);
+        const int S = ihi - ilo + 1;
+        if (S <= 0) continue;
+        const int S4 = (S + 3) & ~3;
+        const int off = ilo - ilo2;
+
+        window_constants(f, p0, n, ilo, S, S4, symE, symF, symG, symPhi);
+        window_fetch(f, p0, n, ilo, S, S4, P, BW, Aw, Bw);
+        drain();  // the previous sub-tile's MMAs have read R and A
+
+        // (A) lattices into R: a warp covers 4 positions x 8 codewords
+        // (conflict-free stores: MN is odd)
+        const int nblk = ((P + 3) >> 2) * (q >> 3);
+        for (int b = warp; b < nblk; b += kThreads / 32) {
+            const int pb = b / (q >> 3), db = b - pb * (q >> 3);
+            const int pl = pb * 4 + (lane >> 3), D = db * 8 + (lane & 7);
+            if (pl >= P) continue;
+            const long long p = p0 + pl;
+            float v[kMaxMN];
+            if (p <= rho) {
+                eval_metric<NB, IB, 0>(f, p, D, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < MN; ++j) v[j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < MN; ++j) {
+                __nv_bfloat16 h, l;
+                tc::split_bf16(v[j], h, l);
+                const uint32_t o = tc::op_offset(D, pl * MN + j, kcR);
+                *reinterpret_cast<__nv_bfloat16 *>(Rhi + o) = h;
+                *reinterpret_cast<__nv_bfloat16 *>(Rlo + o) = l;
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        window_tilt(S, S4, P, BW, Aw, Bw, symE, symF, symG, symPhi);
+        __syncthreads();
+
+        // (C) A chunk by chunk: a thread builds 8 consecutive columns of one row
+        // (one 16-byte store per part); a warp covers 32 consecutive rows
+        for (int c0 = 0; c0 < Kp; c0 += kTcChunk) {
+            const int w = min(kTcChunk, Kp - c0);
+            drain();  // the previous chunk's MMAs have read A
+            for (int u = tid; u < 128 * (w >> 3); u += kThreads) {
+                const int il2 = u & 127, g = u >> 7;
+                const int il = il2 - off;
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    float a[2];
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const int k = c0 + g * 8 + e + t;
+                        a[t] = 0.f;
+                        if (il >= 0 && il < S && k < K) {
+                            const int pl = k / MN, j = k - pl * MN;
+                            a[t] = Aw[pl * S4 + il] * Bw[(pl + j) * S4 + il];
+                        }
+                    }
+                    __nv_bfloat16 h0, l0, h1, l1;
+                    tc::split_bf16(a[0], h0, l0);
+                    tc::split_bf16(a[1], h1, l1);
+                    hw[e >> 1] = (uint32_t)__bfloat16_as_ushort(h0) |
+                                 ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    lw[e >> 1] = (uint32_t)__bfloat16_as_ushort(l0) |
+                                 ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                const uint32_t o = tc::op_offset(il2, g * 8, kcA);
+                *reinterpret_cast<uint4 *>(Ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(Alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
+                const uint32_t rh = smem_u32(Rhi), rl = smem_u32(Rlo);
+                for (int k0 = 0; k0 < w; k0 += 16) {
+                    const uint32_t ao = (uint32_t)(k0 >> 3) * 128u;
+                    const uint32_t ro = (uint32_t)((c0 + k0) >> 3) * 128u;
+                    tc::mma_bf16(tmem, tc::smem_desc(ah + ao, kcA), tc::smem_desc(rh + ro, kcR),
+                                 idesc, issued ? 1u : 0u);
+                    issued = true;
+                    tc::mma_bf16(tmem, tc::smem_desc(ah + ao, kcA), tc::smem_desc(rl + ro, kcR),
+                                 idesc, 1u);
+                    tc::mma_bf16(tmem, tc::smem_desc(al + ao, kcA), tc::smem_desc(rh + ro, kcR),
+                                 idesc, 1u);
+                }
+                tc::commit(&s_bar);
+            }
+            issued = true;  // every thread tracks it (uniform)
+            pending = true;
+        }
+    }
+    drain();
+
+    // (D) the super-tile's sums: TMEM lane il2, columns D, 16 per load; the two
+    // warpgroups take alternate 16-column chunks.  No MMA ran: zeros.
+    const size_t row0 = (size_t)wk.tile * f.S2;
+    const int lg = warp & 3, half = warp >> 2;
+    const int il2 = lg * 32 + lane;
+    const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16);
+    for (int c0 = half * 16; c0 < q; c0 += 32) {
+        float v[16];
+        if (issued) {
+            tc::ld16(ta + (uint32_t)c0, v);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = 0.f;
+        }
+        if (il2 < S2 && !s_fail) {
+            float *dst = f.Lp + (row0 + il2) * q + c0;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) dst[e] = v[e];
+        }
+    }
+    if (tid == 0 && s_fail) atomicMax(f.status, s_fail);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+}  // namespace mdk

@@ -83,6 +83,7 @@ _SIGS = {
     "mapdec_batch_last_launches": (ctypes.c_int64, [_VP]),
     "mapdec_batch_phase_ms": (ctypes.c_int, [_VP, _VP]),
     "mapdec_batch_num_waves": (ctypes.c_int, [_VP]),
+    "mapdec_batch_tc_frames": (ctypes.c_int, [_VP]),
     "mapdec_fp32_fma_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _VP]),
     "mapdec_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
     "mapdec_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
@@ -93,7 +94,8 @@ _SIGS = {
 class Tune(ctypes.Structure):
     """mapdec_tune_t: launch parameters of one (q, n, I) class (0 = planner's choice)."""
     _fields_ = [("P", ctypes.c_int), ("nsub", ctypes.c_int), ("chain_budget_kb", ctypes.c_int),
-                ("chain_stages", ctypes.c_int), ("store_metric", ctypes.c_int)]
+                ("chain_stages", ctypes.c_int), ("store_metric", ctypes.c_int),
+                ("tensor_cores", ctypes.c_int), ("chain_threads", ctypes.c_int)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -289,6 +291,10 @@ def mapdec_batch_phase_ms(b):
 
 def mapdec_batch_num_waves(b):
     return int(load().mapdec_batch_num_waves(b))
+
+
+def mapdec_batch_tc_frames(b):
+    return int(load().mapdec_batch_tc_frames(b))
 
 
 def mapdec_tune_set(q, n, I, tune=None):

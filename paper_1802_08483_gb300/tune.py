@@ -8,7 +8,14 @@ sample of that class's frames and keeps the fastest:
     does not fit and falls back to its own choice);
   * store_metric: keep the receiver metrics R in device memory between the
     forward and the APP producer, or recompute them (decode only);
-  * the recursion CTA's shared-memory budget and bulk-copy stages.
+  * tensor_cores: the producers' contractions on the tensor cores (split
+    bf16, FP32 accumulation) or on the FP32 CUDA cores;
+  * the recursion CTA's shared-memory budget, bulk-copy stages and block size
+    (128, 256 or 512 threads).
+
+The producers' block size is fixed at 256 threads: the tensor-core producers
+split their epilogue over two warpgroups and the CUDA-core producers' register
+tiles are laid out for it; their work per block is tuned through P and nsub.
 
 The producer parameters are searched per class, coordinate by coordinate
 (tile size, super-tile depth, store-or-recompute), each candidate scored by
@@ -32,11 +39,14 @@ import numpy as np
 
 from . import mapdec
 
-FIELDS = ("P", "nsub", "chain_budget_kb", "chain_stages", "store_metric")
-DEFAULT = {"P": 0, "nsub": 0, "chain_budget_kb": 0, "chain_stages": 0, "store_metric": 0}
+FIELDS = ("P", "nsub", "chain_budget_kb", "chain_stages", "store_metric", "tensor_cores",
+          "chain_threads")
+DEFAULT = {k: 0 for k in FIELDS}
 P_CANDIDATES = (0, 1, 2, 4, 8, 16, 32)
 NSUB_CANDIDATES = (0, 2, 4, 8, 16, 32)
-CHAIN_CANDIDATES = ((0, 0), (72, 2), (150, 2), (100, 3))
+TC_CANDIDATES = (0, 2)  # planner's choice (tensor cores where supported), CUDA cores
+# recursion settings: (shared-memory budget KB, stages, threads); 0 = planner's
+CHAIN_CANDIDATES = ((0, 0, 0), (72, 2, 0), (150, 2, 0), (100, 3, 0), (0, 0, 128), (0, 0, 512))
 
 
 def class_of(fr) -> Tuple[int, int, int]:
@@ -91,16 +101,18 @@ def time_frames(frames, reps: int = 3, mem_budget_bytes: int = 0, wall: bool = F
 def tune_class(key, frames, reps: int = 3, log=None,
                p_candidates: Iterable[int] = P_CANDIDATES,
                nsub_candidates: Iterable[int] = NSUB_CANDIDATES,
-               store_candidates: Iterable[int] = (0, 1)) -> dict:
+               store_candidates: Iterable[int] = (0, 1),
+               tc_candidates: Iterable[int] = TC_CANDIDATES) -> dict:
     """Coordinate search of the producer parameters of one class; leaves the
-    winner in the table."""
+    winner in the table.  The kind of producer (tensor or CUDA cores) is chosen
+    first, since the tile sizes that suit it differ."""
     q, n, I = key
     cur = dict(DEFAULT)
     mapdec.mapdec_tune_set(q, n, I, cur)
     base = time_frames(frames, reps)
     best_ms = base
-    for field, values in (("P", p_candidates), ("nsub", nsub_candidates),
-                          ("store_metric", store_candidates)):
+    for field, values in (("tensor_cores", tc_candidates), ("P", p_candidates),
+                          ("nsub", nsub_candidates), ("store_metric", store_candidates)):
         for v in values:
             if v == cur[field]:
                 continue
@@ -117,23 +129,26 @@ def tune_class(key, frames, reps: int = 3, log=None,
 
 
 def tune_chains(entries, frames, reps: int = 2, log=None,
-                chain_candidates: Iterable[Tuple[int, int]] = CHAIN_CANDIDATES) -> dict:
-    """One recursion setting for every class, by the wall time of `frames`."""
-    def set_all(kb, stg):
+                chain_candidates: Iterable[Tuple[int, int, int]] = CHAIN_CANDIDATES) -> dict:
+    """One recursion setting (shared-memory budget, stages, block size) for
+    every class, by the wall time of `frames`."""
+    def set_all(kb, stg, thr):
         for e in entries:
             e["tune"]["chain_budget_kb"], e["tune"]["chain_stages"] = int(kb), int(stg)
+            e["tune"]["chain_threads"] = int(thr)
             mapdec.mapdec_tune_set(e["q"], e["n"], e["I"], e["tune"])
     best = None
-    for kb, stg in chain_candidates:
-        set_all(kb, stg)
+    for cand in chain_candidates:
+        kb, stg, thr = (tuple(cand) + (0,))[:3]
+        set_all(kb, stg, thr)
         ms = time_frames(frames, reps, wall=True)
         if log:
-            log(f"  recursions {kb} KB / {stg} stages: {ms:.1f} ms wall")
+            log(f"  recursions {kb} KB / {stg} stages / {thr or 256} threads: {ms:.1f} ms wall")
         if best is None or ms < best[0]:
-            best = (ms, kb, stg)
-    set_all(best[1], best[2])
-    return {"chain_budget_kb": best[1], "chain_stages": best[2], "wall_ms": best[0],
-            "sample_frames": len(frames)}
+            best = (ms, kb, stg, thr)
+    set_all(best[1], best[2], best[3])
+    return {"chain_budget_kb": best[1], "chain_stages": best[2], "chain_threads": best[3],
+            "wall_ms": best[0], "sample_frames": len(frames)}
 
 
 def tune(frames, sample: int = 48, chain_sample: int = 1024, reps: int = 3, log=None,

@@ -89,7 +89,8 @@ def test_forward_without_grad_skips_the_adjoint():
     import torch
     from paper_1802_08483_gb300.autograd import frame_loglik
     rng = np.random.default_rng(504)
-    fr = synth.make_frame(rng, 16, 8, 80, 2, 24, 0.04, 0.03, 0.01, dirichlet=True)
+    # large enough that the gradient scratch (about 12 MB) shows in the free memory
+    fr = synth.make_frame(rng, 16, 8, 1000, 2, 60, 0.01, 0.01, 0.005, dirichlet=True)
     dec = mapdec.Decoder.for_frame(fr)
     dec.decode(fr.rx, fr.priors)  # loads the decode kernels
     pri = torch.tensor(fr.priors, device="cuda")

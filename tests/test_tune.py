@@ -17,7 +17,8 @@ def _lib():
 
 def test_table_set_get_remove():
     mapdec.mapdec_tune_clear()
-    t = {"P": 8, "nsub": 4, "chain_budget_kb": 72, "chain_stages": 2, "store_metric": 1}
+    t = {"P": 8, "nsub": 4, "chain_budget_kb": 72, "chain_stages": 2, "store_metric": 1,
+         "tensor_cores": 2, "chain_threads": 512}
     mapdec.mapdec_tune_set(64, 12, 2, t)
     assert mapdec.mapdec_tune_get(64, 12, 2) == t
     assert mapdec.mapdec_tune_get(64, 12, 3) is None
@@ -49,6 +50,9 @@ def test_json_round_trip(tmp_path):
     tune.load(str(path))
     assert mapdec.mapdec_tune_get(16, 10, 2)["P"] == 16
     assert mapdec.mapdec_tune_get(2, 4, 2)["store_metric"] == 1
+    # fields missing from an older table read as the planner's choice
+    assert mapdec.mapdec_tune_get(2, 4, 2)["tensor_cores"] == 0
+    assert mapdec.mapdec_tune_get(2, 4, 2)["chain_threads"] == 0
     mapdec.mapdec_tune_clear()
 
 
