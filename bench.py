@@ -92,6 +92,22 @@ def lattice_counts(frames) -> dict:
     return {"evaluated": ev, "paper_grid": grid, "ratio": grid / ev if ev else None}
 
 
+def pipe_flops(fr, tc_bits: int = 0) -> dict:
+    """Algorithmic flops of one frame by phase and by the pipe that runs them:
+    the contractions of a frame whose producers run on the tensor cores
+    (tc_bits: bit 0 forward producer, bit 1 APP producer) count on the tensor
+    pipe, everything else on the FP32 pipe.  "executed_fp32" adds the lattices
+    the APP producer recomputes."""
+    ff = frame_flops(fr)
+    w = 2 * fr.q * ff["V"]
+    out = {"forward": {"fp32": ff["lattice"] + (0 if tc_bits & 1 else w),
+                       "tensor": w if tc_bits & 1 else 0},
+           "chains": {"fp32": ff["chains"], "tensor": 0},
+           "backward": {"fp32": 0 if tc_bits & 2 else w, "tensor": w if tc_bits & 2 else 0}}
+    out["backward"]["executed_fp32"] = out["backward"]["fp32"] + ff["backward_recompute"]
+    return out
+
+
 def frame_flops(fr) -> dict:
     """FP32 flops per phase for one frame (one FMA = 2 flops).
 
@@ -503,13 +519,21 @@ def main():
     frames = [synth.config_frame(3, frame_offset + f) for f in range(args.frames)]
     gen_s = time.time() - t0
     bits_per_step = sum(f.info_bits for f in frames)
-    flops = {"forward": 0, "chains": 0, "backward": 0, "lattice": 0, "V": 0}
+    flops = {"forward": 0, "chains": 0, "backward": 0, "backward_recompute": 0, "lattice": 0,
+             "V": 0}
     for f in frames:
         for k, v in frame_flops(f).items():
             flops[k] += v
 
     b = mapdec.Batch(frames, flags=mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_TIMING,
                      mem_budget_bytes=int(args.mem_budget_gb * (1 << 30)))
+    tc_count, tc_bits = mapdec.mapdec_batch_tc_frames(b.b, b.nf)
+    pipes = {k: {"fp32": 0, "tensor": 0} for k in ("forward", "chains", "backward")}
+    pipes["backward"]["executed_fp32"] = 0
+    for f, bits in zip(frames, tc_bits):
+        for k, v in pipe_flops(f, int(bits)).items():
+            for kk, vv in v.items():
+                pipes[k][kk] += vv
     rx_all, pr_all = b.concat_inputs()
     # stage inputs into the batch's resident device buffers (one decode call)
     st, app0, ll0 = b.decode(rx_all, pr_all)
@@ -567,10 +591,18 @@ def main():
     names = list(mapdec.PHASES)
     dom = int(np.argmax(phase_ms))
     dom_name = names[dom]
-    dom_flops = flops.get(dom_name, 0)
-    dom_exec = dom_flops + (flops["backward_recompute"] if dom_name == "backward" else 0)
     sec = phase_ms[dom] / 1e3
-    achieved = dom_flops / sec / 1e12 if sec > 0 else 0.0
+    # the dominant phase's algorithmic work on each pipe; the bound is the pipe
+    # it uses the larger fraction of
+    tensor_peak = float(peaks.get("bf16_tflops_sustained", 1709.5))  # timed inside a long step
+    pf = pipes.get(dom_name, {"fp32": 0, "tensor": 0})
+    fp32_t = pf["fp32"] / sec / 1e12 if sec > 0 else 0.0
+    tens_t = pf["tensor"] / sec / 1e12 if sec > 0 else 0.0
+    fp32_frac = fp32_t / fp32_peak if fp32_peak else 0.0
+    tens_frac = tens_t / tensor_peak if tensor_peak else 0.0
+    tensor_bound = tens_frac > fp32_frac
+    achieved = tens_t if tensor_bound else fp32_t
+    peak = tensor_peak if tensor_bound else fp32_peak
     traffic = phase_traffic(dom_name)
     try:
         probe = mapdec.mapdec_fp32_fma_peak(stream.cuda_stream)
@@ -578,22 +610,33 @@ def main():
         probe = None
     total_alg = flops["forward"] + flops["chains"] + flops["backward"]
     step_tflops = total_alg / (ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak if fp32_peak else None, "traffic": traffic,
+    step_fp32 = sum(pipes[k]["fp32"] for k in ("forward", "chains", "backward"))
+    step_tens = sum(pipes[k]["tensor"] for k in ("forward", "chains", "backward"))
+    roofline = {"bound": "tensor" if tensor_bound else "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                "traffic": traffic,
                 "kernel": f"{dom_name} phase ({PHASE_KERNELS.get(dom_name, '')})",
                 "flops": "algorithmic: each lattice once, the W and APP contractions (2q per "
                          "valid transition each), the recursions (2 per transition each); the "
                          "backward phase's own work is the APP contraction",
-                "executed": {"tflops": dom_exec / sec / 1e12 if sec > 0 else 0.0,
-                             "note": "adds the lattices the APP producer recomputes "
-                                     "(executed, not algorithmic)"},
+                "pipes": {"fp32": {"achieved": fp32_t, "peak": fp32_peak, "frac": fp32_frac,
+                                   "peak_source": f"{props.multi_processor_count} SMs x 128 "
+                                                  f"FP32 lanes x 2 x {sm_max:.0f} MHz",
+                                   "peak_probe": probe,
+                                   "frac_of_probe": fp32_t / probe if probe else None},
+                          "tensor": {"achieved": tens_t, "peak": tensor_peak, "frac": tens_frac,
+                                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained "
+                                                    "(cuBLAS bf16, of measured)",
+                                     "executed_products": 3,
+                                     "note": "split bf16: three MMAs per algorithmic product"}},
+                "executed_fp32": {"tflops": (pf.get("executed_fp32", pf["fp32"]) / sec / 1e12)
+                                  if sec > 0 else 0.0,
+                                  "note": "adds the lattices the APP producer recomputes "
+                                          "(executed, not algorithmic)"},
                 "step": {"algorithmic_tflops": step_tflops,
-                         "frac": step_tflops / fp32_peak if fp32_peak else None},
-                "phase_ms": {names[k]: round(float(phase_ms[k]), 3) for k in range(5)},
-                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                               f"{sm_max:.0f} MHz",
-                "peak_probe": probe,
-                "frac_of_probe": achieved / probe if probe else None}
+                         "fp32_frac": step_fp32 / (ms / 1e3) / 1e12 / fp32_peak,
+                         "tensor_frac": step_tens / (ms / 1e3) / 1e12 / tensor_peak},
+                "phase_ms": {names[k]: round(float(phase_ms[k]), 3) for k in range(5)}}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -640,6 +683,8 @@ def main():
                        "frames_per_gpu": args.frames, "info_bits_per_gpu_step": bits_per_step,
                        "l2": "inputs and scratch larger than L2 (no flush needed)",
                        "waves": mapdec.mapdec_batch_num_waves(b.b),
+                       "tensor_core_frames": {"forward": int(tc_count),
+                                              "app": int(sum(1 for x in tc_bits if x & 2))},
                        "tuning": tuning,
                        "parallelism": f"frames sharded, {n_gpus} GPU(s), no collective",
                        "gen_seconds": round(gen_s, 1)},

@@ -145,6 +145,16 @@ typedef struct {
     double Pi, Pd, Ps;
     const uint8_t *codebook; /* q*n bytes, host or device; copied at create */
     int64_t rx_len;          /* rho of this frame */
+    int codebook_per_symbol; /* 0: one codebook for every symbol; 1: one per symbol
+                                (the constituent encodings C_i of Sec. II-A):
+                                codebook holds N*q*n bytes, symbol i's q*n at offset
+                                i*q*n, each with distinct rows; q <= 256.  The
+                                receiver metric then depends on the symbol, so the
+                                producers evaluate the paper's (i, m', D) grid of
+                                lattices (no position dedupe): about M/n times the
+                                work of one codebook.  Not with
+                                MAPDEC_BATCH_SEGMENTED or mapdec_decode_noalloc
+                                (MAPDEC_ERR_UNSUPPORTED). */
 } mapdec_frame_desc_t;
 
 /*
@@ -341,15 +351,19 @@ int mapdec_tune_clear(void);
 int mapdec_batch_num_waves(mapdec_batch_t *b);
 
 /*
- * Number of the batch's frames whose contractions run on the tensor cores
- * (tcgen05, bf16 operands split into high and low parts, FP32 accumulation;
- * an implementation choice, not in the paper).  The planner picks them for
- * classes with q a multiple of 16 up to 64 and n >= 4 (the other frames use the
- * FP32 CUDA-core producers); the environment variable MAPDEC_TC=0, read when a
- * batch is created, keeps every frame on the CUDA-core producers.  -1 for a
- * NULL batch.
+ * Frames whose contractions run on the tensor cores (tcgen05, bf16 operands
+ * split into high and low parts, FP32 accumulation; an implementation choice,
+ * not in the paper).  The planner picks them in decode batches for classes
+ * with q a multiple of 16 up to 64 and n >= 4 whose tiles fit (the other
+ * frames, and every frame of a MAPDEC_BATCH_GRAD batch, use the FP32 CUDA-core
+ * producers); the environment variables MAPDEC_TC=0 and MAPDEC_TC_BWD=0, read
+ * when a batch is created, keep every frame's producers, or its APP producer,
+ * on the CUDA cores.  If flags is not NULL it receives one int per frame: bit 0
+ * set when the forward producer (W contraction) runs on the tensor cores,
+ * bit 1 when the APP producer does.  Returns the number of frames with bit 0
+ * set, or -1 for a NULL batch.
  */
-int mapdec_batch_tc_frames(mapdec_batch_t *b);
+int mapdec_batch_tc_frames(mapdec_batch_t *b, int *flags);
 
 /*
  * Measured FP32 FMA throughput of the current device in TFLOP/s (2 flops per

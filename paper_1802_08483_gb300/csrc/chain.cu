@@ -476,6 +476,7 @@ constexpr int kFinChunk = 64;
 __device__ __forceinline__ long long lp_row(const FrameDev &f, long long myrow, int t, int tlo,
                                             int i) {
     const long long cached = __shfl_sync(0xffffffffu, myrow, t & 31);
+    if (f.ps) return (long long)tlo + t;  // per-symbol producers: rows i*psT .. i*psT+psT-1
     if (t < 32) return cached;
     int ilo, ihi;
     super_symbols(f, tlo + t, ilo, ihi);
@@ -504,10 +505,14 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FrameDev *__rest
         long long plo = (long long)n * i - xmax, phi = (long long)n * i + xmax;
         if (plo < 0) plo = 0;
         if (phi > f.rho) phi = f.rho;
-        const int tlo = (int)(plo / P2), thi = (int)(phi / P2);
+        int tlo = (int)(plo / P2), thi = (int)(phi / P2);
+        if (f.ps) {  // one row per work item (symbol, chunk of start states)
+            tlo = i * f.psT;
+            thi = tlo + f.psT - 1;
+        }
         // lane l holds the Lp row offset of super-tile tlo + l for this symbol
         long long myrow = 0;
-        if (tlo + lane <= thi) {
+        if (!f.ps && tlo + lane <= thi) {
             int ilo, ihi;
             super_symbols(f, tlo + lane, ilo, ihi);
             myrow = (long long)(tlo + lane) * f.S2 + (i - ilo);

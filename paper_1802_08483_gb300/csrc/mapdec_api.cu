@@ -303,18 +303,17 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     f.chainStages = stages;
 }
 
-// Forward tile of the tensor-core producer: the most positions whose
-// (position, length) rows fit two 128-row MMA tiles, with at most 256 symbols
-// per tile (the MMA's N) and the shared memory within the two-CTA budget.
-// Sets Pf, Sf, Tf; false if no tile fits (the CUDA-core producer is used).
+// Forward tile of the tensor-core producer: up to one lattice per thread
+// (Pf <= 256 / q positions), at most 256 symbols from the 8-aligned first one
+// (the MMA's N), the shared memory within the two-CTA budget.  Sets Pf, Sf,
+// Tf; false if no tile fits (the CUDA-core producer is used).
 bool plan_fwd_tc(FrameDev &f) {
     if (!fwd_tc_supported(f.q, f.n, f.I)) return false;
-    for (int P = 32; P >= 1; --P) {
-        if (P * f.MN > 256) continue;
+    for (int P = std::max(1, 256 / f.q); P >= 1; --P) {
         FrameDev t = f;
         t.Pf = P;
         t.Sf = (int)std::min<long long>(((long long)P - 1 + 2LL * f.xmax) / f.n + 2, f.N);
-        if (((t.Sf + 15) & ~15) > 256) continue;
+        if (((t.Sf + 7 + 15) & ~15) > 256) continue;
         if (fwd_tc_smem_bytes(t) > kFwdSmemBudget) continue;
         f.Pf = t.Pf;
         f.Sf = t.Sf;
@@ -353,6 +352,7 @@ bool plan_bwd_tc(FrameDev &f) {
 
 size_t frame_scratch_floats(const FrameDev &f, bool grad) {
     size_t s = 0;
+    if (f.Pgroups) s += rup(prior_split_bytes(f) / 4, 64);  // priors split for the tensor cores
     s += rup((size_t)f.N * f.wblk + 16, 64);             // W (+ tail slack for bulk copies)
     s += rup((size_t)(f.N + 1) * f.Mp, 64) * 2;          // alpha, beta
     s += rup((size_t)f.T2 * f.S2 * f.q, 64);             // Lp
@@ -372,6 +372,7 @@ size_t frame_scratch_floats_seg(const FrameDev &f, int K, int S, bool grad) {
     const int T2s = seg_supertiles(f, K);
     const int cps = finalize_chunks(K);
     size_t s = 0;
+    if (f.Pgroups) s += rup(prior_split_bytes(f) / 4, 64);  // priors split for the tensor cores
     s += 2 * rup((size_t)K * f.wblk + 16, 64);           // W of a segment, two buffers
     s += 4 * rup((size_t)(K + 1) * f.Mp, 64);            // alpha, beta rows of a segment, two buffers
     s += rup((size_t)T2s * f.S2 * f.q, 64);              // Lp of one segment
@@ -397,11 +398,13 @@ double frame_cost(const FrameDev &f) {
 using ClassKey = std::tuple<int, int, int>;  // n, I, tensor-core bits (kTcFwd | kTcBwd)
 
 constexpr int kTcFwd = 1, kTcBwd = 2;  // ClassKey / FrameHost tensor-core bits
+constexpr int kPerSym = 4;             // ClassKey: per-symbol-codebook producers
 
 struct ClassLaunch {
     int n, I;
     bool tc = false;   // forward producer on the tensor cores (producers_tc.cuh)
     bool tcb = false;  // APP producer on the tensor cores
+    bool ps = false;   // per-symbol-codebook producers (producers_ps.cuh)
     Work *d_fwd = nullptr; int nfwd = 0; size_t smem_fwd = 0;
     Work *d_bwd = nullptr; int nbwd = 0; size_t smem_bwd = 0;
 };
@@ -429,6 +432,7 @@ struct Wave {
     const uint8_t **d_rxptr = nullptr;
     uint32_t **d_rxwptr = nullptr;
     long long max_words = 0;
+    long long prior_split_threads = 0;  // the largest tensor-core frame's k_prior_split work
 };
 
 }  // namespace
@@ -576,6 +580,7 @@ void build_segments(mapdec_batch *b, Wave &w, const std::vector<FrameDev> &devs,
             c.I = std::get<1>(kv.first);
             c.tc = (std::get<2>(kv.first) & kTcFwd) != 0;
             c.tcb = (std::get<2>(kv.first) & kTcBwd) != 0;
+            c.ps = (std::get<2>(kv.first) & kPerSym) != 0;
             std::vector<Work> fw, bwk;
             for (int k : kv.second) {
                 const FrameHost &h = b->fr[w.f0 + k];
@@ -587,7 +592,9 @@ void build_segments(mapdec_batch *b, Wave &w, const std::vector<FrameDev> &devs,
                 for (long long t = plo / f.Pf; t <= phi / f.Pf; ++t) fw.push_back({k, (int)t});
                 for (long long t = plo / P2; t <= phi / P2; ++t) bwk.push_back({k, (int)t});
                 c.smem_fwd = std::max(c.smem_fwd, c.tc ? fwd_tc_smem_bytes(f) : fwd_smem_bytes(f));
-                c.smem_bwd = std::max(c.smem_bwd, c.tcb ? bwd_tc_smem_bytes(f) : bwd_smem_bytes(f, b->grad));
+                c.smem_bwd = std::max(c.smem_bwd, c.ps    ? bwd_ps_smem_bytes(f, b->grad)
+                                                  : c.tcb ? bwd_tc_smem_bytes(f)
+                                                          : bwd_smem_bytes(f, b->grad));
             }
             upload(fw, c.d_fwd, c.nfwd);
             upload(bwk, c.d_bwd, c.nbwd);
@@ -611,8 +618,32 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         const long long tau = (long long)h.d.n * h.d.N;
         if (h.d.rx_len < 0) return MAPDEC_ERR_ARG;
         if (std::llabs(h.d.rx_len - tau) > h.d.xmax) return MAPDEC_ERR_DRIFT_RANGE;
-        st = pack_codebook(h.d.codebook, h.d.q, h.d.n, h.cw);
-        if (st) return st;
+        const bool per_sym = h.d.codebook_per_symbol != 0;
+        if (h.d.codebook_per_symbol != 0 && h.d.codebook_per_symbol != 1) return MAPDEC_ERR_ARG;
+        if (per_sym && (h.d.q > kPsMaxQ || (flags & MAPDEC_BATCH_SEGMENTED)))
+            return MAPDEC_ERR_UNSUPPORTED;
+        if (per_sym) {
+            // N codebooks of q*n bytes, each injective (Sec. II-A)
+            if (!h.d.codebook) return MAPDEC_ERR_ARG;
+            const size_t cbn = (size_t)h.d.q * h.d.n;
+            std::vector<uint8_t> all((size_t)h.d.N * cbn);
+            if (is_device_ptr(h.d.codebook)) {
+                CK(cudaMemcpy(all.data(), h.d.codebook, all.size(), cudaMemcpyDeviceToHost));
+            } else {
+                std::memcpy(all.data(), h.d.codebook, all.size());
+            }
+            h.cw.clear();
+            h.cw.reserve((size_t)h.d.N * h.d.q);
+            std::vector<uint32_t> one;
+            for (int sym = 0; sym < h.d.N; ++sym) {
+                st = pack_codebook(all.data() + (size_t)sym * cbn, h.d.q, h.d.n, one);
+                if (st) return st;
+                h.cw.insert(h.cw.end(), one.begin(), one.end());
+            }
+        } else {
+            st = pack_codebook(h.d.codebook, h.d.q, h.d.n, h.cw);
+            if (st) return st;
+        }
         h.d.codebook = nullptr;
         const bool plain = (flags & MAPDEC_BATCH_PLAIN) != 0;
         mapdec_tune_t tu{};
@@ -627,12 +658,26 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         // (about 2^-16 per product) leaves it 3e-4 off relative on small
         // gradients, where the FP32 W meets 1e-4.  MAPDEC_TC=0 keeps every frame
         // on the CUDA-core producers (A/B tests).
-        bool tc_on = !(tuned && tu.tensor_cores == 2);
+        bool tc_on = tuned && tu.tensor_cores == 1;
         if (const char *e = std::getenv("MAPDEC_TC")) tc_on = std::atoi(e) != 0;
         if (tuned && (tu.chain_threads == 128 || tu.chain_threads == 256 ||
                       tu.chain_threads == 512))
             b->chain_threads = tu.chain_threads;
+        if (per_sym) {
+            // per-symbol producers: work items (symbol, chunk of psC start states),
+            // one APP partial row each (T2 * S2 rows with S2 = 1)
+            FrameDev &f = h.dev;
+            f.ps = 1;
+            f.psC = ps_chunk_states(f.q, f.M);
+            f.psT = (f.M + f.psC - 1) / f.psC;
+            f.Tf = f.N * f.psT;
+            f.T2 = f.N * f.psT;
+            f.S2 = 1;
+            h.store = false;
+            tc_on = false;
+        }
         h.tc = tc_on && !h.store && !b->grad && plan_fwd_tc(h.dev);
+        if (h.tc) h.dev.Pgroups = prior_split_groups(h.dev);
         bool tcb_on = tc_on;
         if (const char *e = std::getenv("MAPDEC_TC_BWD")) tcb_on = tcb_on && std::atoi(e) != 0;
         h.tcb = tcb_on && h.tc && !b->grad && plan_bwd_tc(h.dev);
@@ -658,7 +703,7 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         h.rxw_off = b->rxw_total;
         b->rxw_total += (h.d.rx_len + 31) / 32 + 4;
         h.cw_off = b->cw_total;
-        b->cw_total += h.d.q;
+        b->cw_total += (int64_t)h.cw.size();
     }
     // resident buffers
     b->d_rx = (uint8_t *)b->dalloc(b->rx_total + 64);
@@ -730,6 +775,11 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             f.priors = b->d_priors + h.sym_off;
             float *base = b->d_scratch + off;
             size_t o = 0;
+            f.Pbuf = nullptr;
+            if (f.Pgroups) {
+                f.Pbuf = reinterpret_cast<unsigned char *>(base + o);
+                o += rup(prior_split_bytes(f) / 4, 64);
+            }
             if (!segmented) {
                 f.W = base + o; o += rup((size_t)f.N * f.wblk + 16, 64);
                 f.alpha = base + o; o += rup((size_t)(f.N + 1) * f.Mp, 64);
@@ -781,8 +831,12 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             rxp.push_back(b->d_rx + h.rx_off);
             rxwp.push_back(b->d_rxw + h.rxw_off);
             w.max_words = std::max<long long>(w.max_words, (h.d.rx_len + 31) / 32 + 3);
-            byclass[ClassKey{h.d.n, h.d.I, (h.tc ? kTcFwd : 0) | (h.tcb ? kTcBwd : 0)}].push_back(
-                i - w.f0);
+            if (f.Pgroups)
+                w.prior_split_threads = std::max<long long>(
+                    w.prior_split_threads, (long long)f.Pgroups * (f.q / 8) * 8);
+            byclass[ClassKey{h.d.n, h.d.I, (h.tc ? kTcFwd : 0) | (h.tcb ? kTcBwd : 0) |
+                                               (f.ps ? kPerSym : 0)}]
+                .push_back(i - w.f0);
         }
         const int nw = w.f1 - w.f0;
         w.d_frames = (FrameDev *)b->dalloc(sizeof(FrameDev) * nw);
@@ -823,13 +877,16 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             c.I = std::get<1>(kv.first);
             c.tc = (std::get<2>(kv.first) & kTcFwd) != 0;
             c.tcb = (std::get<2>(kv.first) & kTcBwd) != 0;
+            c.ps = (std::get<2>(kv.first) & kPerSym) != 0;
             std::vector<Work> fw, bw;
             for (int k : kv.second) {
                 const FrameDev &f = devs[k];
                 for (int t = 0; t < f.Tf; ++t) fw.push_back({k, t});
                 for (int t = 0; t < f.T2; ++t) bw.push_back({k, t});
                 c.smem_fwd = std::max(c.smem_fwd, c.tc ? fwd_tc_smem_bytes(f) : fwd_smem_bytes(f));
-                c.smem_bwd = std::max(c.smem_bwd, c.tcb ? bwd_tc_smem_bytes(f) : bwd_smem_bytes(f, b->grad));
+                c.smem_bwd = std::max(c.smem_bwd, c.ps    ? bwd_ps_smem_bytes(f, b->grad)
+                                                  : c.tcb ? bwd_tc_smem_bytes(f)
+                                                          : bwd_smem_bytes(f, b->grad));
             }
             c.nfwd = (int)fw.size();
             c.nbwd = (int)bw.size();
@@ -879,6 +936,10 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         mark(w, 0, 0, st);
         CK(launch_pack(wv.d_frames, wv.d_rxptr, wv.d_rxwptr, wv.f1 - wv.f0, wv.max_words, st));
         ++launches;
+        if (wv.prior_split_threads > 0) {
+            CK(launch_prior_split(wv.d_frames, wv.f1 - wv.f0, wv.prior_split_threads, st));
+            ++launches;
+        }
         mark(w, 0, 1, st);
     }
     CK(cudaEventRecord(fork, st));
@@ -887,8 +948,9 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         Wave &wv = b->waves[w];
         mark(w, 1, 0, st);
         for (auto &c : wv.cls) {
-            CK(c.tc ? launch_fwd_tc(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st)
-                    : launch_fwd(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
+            CK(c.ps   ? launch_fwd_ps(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, st)
+               : c.tc ? launch_fwd_tc(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st)
+                      : launch_fwd(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st));
             ++launches;
         }
         mark(w, 1, 1, st);
@@ -907,8 +969,9 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         CK(cudaStreamWaitEvent(st, b->dep[2 * w + 1], 0));
         mark(w, 3, 0, st);
         for (auto &c : wv.cls) {
-            CK(c.tcb ? launch_bwd_tc(c.n, c.I, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st)
-                     : launch_bwd(c.n, c.I, grad, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
+            CK(c.ps    ? launch_bwd_ps(c.n, c.I, grad, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st)
+               : c.tcb ? launch_bwd_tc(c.n, c.I, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st)
+                       : launch_bwd(c.n, c.I, grad, wv.d_frames, c.d_bwd, c.nbwd, c.smem_bwd, st));
             ++launches;
         }
         mark(w, 3, 1, st);
@@ -958,6 +1021,10 @@ int64_t enqueue_run_seg(mapdec_batch *b, bool grad, cudaStream_t st) {
         mark(w, 0, 0, st);
         CK(launch_pack(wv.d_frames, wv.d_rxptr, wv.d_rxwptr, nw, wv.max_words, st));
         ++launches;
+        if (wv.prior_split_threads > 0) {
+            CK(launch_prior_split(wv.d_frames, nw, wv.prior_split_threads, st));
+            ++launches;
+        }
         mark(w, 0, 1, st);
         CK(cudaEventRecord(fork, st));
         CK(cudaStreamWaitEvent(cs, fork, 0));
@@ -1377,10 +1444,14 @@ int mapdec_batch_phase_ms(mapdec_batch_t *b, double *ms) {
 
 int mapdec_batch_num_waves(mapdec_batch_t *b) { return b ? (int)b->waves.size() : -1; }
 
-int mapdec_batch_tc_frames(mapdec_batch_t *b) {
+int mapdec_batch_tc_frames(mapdec_batch_t *b, int *flags) {
     if (!b) return -1;
     int c = 0;
-    for (const auto &h : b->fr) c += h.tc ? 1 : 0;
+    for (size_t k = 0; k < b->fr.size(); ++k) {
+        const FrameHost &h = b->fr[k];
+        c += h.tc ? 1 : 0;
+        if (flags) flags[k] = (h.tc ? 1 : 0) | (h.tcb ? 2 : 0);
+    }
     return c;
 }
 
@@ -1438,6 +1509,7 @@ int mapdec_create(mapdec_t **out, int q, int n, const uint8_t *codebook, int N, 
     d.Pi = Pi; d.Pd = Pd; d.Ps = Ps;
     d.codebook = h->codebook.data();
     d.rx_len = h->rho_max;
+    d.codebook_per_symbol = 0;
     st = mapdec_batch_create(&h->b, &d, 1, MAPDEC_BATCH_PLAIN | MAPDEC_BATCH_EXTRINSIC, 0);
     if (st) {
         delete h;
@@ -1466,9 +1538,11 @@ void retarget_single(mapdec_batch *b, int64_t rho, bool ext) {
     FrameDev &f = h.dev;
     h.d.rx_len = rho;
     f.rho = rho;
-    f.T = (int)((rho + 1 + f.P - 1) / f.P);
-    f.T2 = (f.T + f.nsub - 1) / f.nsub;
-    f.Tf = (int)((rho + 1 + f.Pf - 1) / f.Pf);
+    if (!f.ps) {  // per-symbol work items do not depend on rho
+        f.T = (int)((rho + 1 + f.P - 1) / f.P);
+        f.T2 = (f.T + f.nsub - 1) / f.nsub;
+        f.Tf = (int)((rho + 1 + f.Pf - 1) / f.Pf);
+    }
     f.ext = ext ? b->d_ext : nullptr;
     b->rx_total = rho;
     Wave &w = b->waves[0];
@@ -1491,6 +1565,7 @@ static int ensure_single(mapdec_t *h, int64_t rho, bool grad, bool ext = false) 
         d.Pi = h->Pi; d.Pd = h->Pd; d.Ps = h->Ps;
         d.codebook = h->codebook.data();
         d.rx_len = h->rho_max;
+        d.codebook_per_symbol = 0;
         int st = mapdec_batch_create(&h->bg, &d, 1, MAPDEC_BATCH_PLAIN | MAPDEC_BATCH_GRAD, 0);
         if (st) return st;
         h->bg->stream = h->stream;
@@ -1567,6 +1642,7 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     const mapdec_frame_desc_t &d = *frame;
     int st = validate(d.q, d.n, d.N, d.Pi, d.Pd, d.Ps, d.I, d.xmax);
     if (st) return st;
+    if (d.codebook_per_symbol) return MAPDEC_ERR_UNSUPPORTED;
     if (d.q > kStaticMaxQ) return MAPDEC_ERR_TOO_LARGE;
     const long long tau = (long long)d.n * d.N;
     if (d.rx_len < 0) return MAPDEC_ERR_ARG;

@@ -23,6 +23,7 @@ constexpr int TEST_SKIP_FIRST_COPY = 1;  // a recursion's first copy is never is
 constexpr int kMaxI = 7;        // insertion cap supported by the kernels
 constexpr int kMaxMN = 64;      // n(I+1) + 1 <= 64 (received window fits 64 bits)
 constexpr int kThreads = 256;   // producer block size
+constexpr int kPsMaxQ = 256;    // codewords per symbol of the per-symbol-codebook producers
 
 // Status codes shared with the C ABI (mapdec.h).
 enum : int {
@@ -53,6 +54,13 @@ struct FrameDev {
                   // tensor-core forward producer picked its own)
     int Sf;       // max symbols touched by one forward tile
     int Tf;       // forward tiles: ceil((rho+1)/Pf)
+    int ps;       // 1: one codebook per symbol (cw holds N*q words, C_i(D) at i*q + D);
+                  // the producers are the per-symbol kernels, work item = i*psT + chunk
+    int psC;      // per-symbol producers: start states per work item
+    int psT;      // per-symbol producers: work items per symbol, ceil(M / psC)
+    int Pgroups;  // tensor-core forward producer: 8-row groups of Pbuf
+    unsigned char *Pbuf;  // the priors split into three bf16 pieces in that
+                          // producer's operand layout (k_prior_split), or null
     int nsub;     // sub-tiles per backward super-tile
     int S2;       // max symbols touched by one super-tile (rows of Lp per super-tile)
     int T2;       // backward super-tiles: ceil(T / nsub)

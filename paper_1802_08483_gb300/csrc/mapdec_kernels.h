@@ -49,8 +49,23 @@ size_t fwd_smem_bytes(const FrameDev &f);
 // its shared memory, and its launch.
 bool fwd_tc_supported(int q, int n, int I);
 size_t fwd_tc_smem_bytes(const FrameDev &f);
+// The priors of a frame split into bf16 pieces in the tensor-core operand
+// layout (k_prior_split): 8-row groups allocated, bytes, and the launch (one
+// thread per group, 8-column chunk and row; max_threads = the largest frame's).
+inline int prior_split_groups(const FrameDev &f) { return (f.N + 16 + 7) / 8; }
+size_t prior_split_bytes(const FrameDev &f);
+cudaError_t launch_prior_split(const FrameDev *frames, int nframes, long long max_threads,
+                               cudaStream_t st);
 cudaError_t launch_fwd_tc(int n, int I, const FrameDev *frames, const Work *work, int nwork,
                           size_t smem, cudaStream_t st);
+// Per-symbol-codebook producers (producers_ps.cuh): any (n, I) the lattices
+// support, q <= 256; work items (frame, symbol * psT + chunk).
+cudaError_t launch_fwd_ps(int n, int I, const FrameDev *frames, const Work *work, int nwork,
+                          cudaStream_t st);
+cudaError_t launch_bwd_ps(int n, int I, bool grad, const FrameDev *frames, const Work *work,
+                          int nwork, size_t smem, cudaStream_t st);
+size_t bwd_ps_smem_bytes(const FrameDev &f, bool grad);
+int ps_chunk_states(int q, int M);  // start states per work item
 // Tensor-core APP producer (decode mode): same class rule, S2 <= 128.
 size_t bwd_tc_smem_bytes(const FrameDev &f);
 cudaError_t launch_bwd_tc(int n, int I, const FrameDev *frames, const Work *work, int nwork,
@@ -86,7 +101,13 @@ int finalize_chunks(int N);  // work items (frame, chunk) per frame
     cudaError_t launch_fwd_tc_I##IB(int n, const FrameDev *frames, const Work *work,         \
                                     int nwork, size_t smem, cudaStream_t st);                \
     cudaError_t launch_bwd_tc_I##IB(int n, const FrameDev *frames, const Work *work,         \
-                                    int nwork, size_t smem, cudaStream_t st);
+                                    int nwork, size_t smem, cudaStream_t st);                \
+    cudaError_t launch_fwd_ps_I##IB(int n, const FrameDev *frames, const Work *work,         \
+                                    int nwork, cudaStream_t st);                             \
+    cudaError_t launch_bwd_ps_I##IB##_plain(int n, const FrameDev *frames, const Work *work, \
+                                            int nwork, size_t smem, cudaStream_t st);        \
+    cudaError_t launch_bwd_ps_I##IB##_grad(int n, const FrameDev *frames, const Work *work,  \
+                                           int nwork, size_t smem, cudaStream_t st);
 MAPDEC_DECLARE_I(1)
 MAPDEC_DECLARE_I(2)
 MAPDEC_DECLARE_I(3)

@@ -21,4 +21,13 @@ cudaError_t launch_bwd_tc_I2(int n, const FrameDev *frames, const Work *work, in
     }
 }
 
+cudaError_t launch_bwd_ps_I2_plain(int n, const FrameDev *frames, const Work *work,
+                                  int nwork, size_t smem, cudaStream_t st) {
+    const bool grad = false;
+    switch (n) {
+        MAPDEC_FOR_N(MAPDEC_CASE_BWDPS)
+        default: return cudaErrorNotSupported;
+    }
+}
+
 }  // namespace mdk

@@ -27,4 +27,12 @@ cudaError_t launch_rmetric_I3(int n, const FrameDev *frame, long long nthreads, 
     }
 }
 
+cudaError_t launch_fwd_ps_I3(int n, const FrameDev *frames, const Work *work, int nwork,
+                             cudaStream_t st) {
+    switch (n) {
+        MAPDEC_FOR_N(MAPDEC_CASE_FWDPS)
+        default: return cudaErrorNotSupported;
+    }
+}
+
 }  // namespace mdk

@@ -19,4 +19,13 @@ cudaError_t launch_bwd_I3(int n, bool g, const FrameDev *frames, const Work *wor
              : launch_bwd_I3_plain(n, frames, work, nwork, smem, st);
 }
 
+cudaError_t launch_bwd_ps_I3_grad(int n, const FrameDev *frames, const Work *work,
+                                  int nwork, size_t smem, cudaStream_t st) {
+    const bool grad = true;
+    switch (n) {
+        MAPDEC_FOR_N(MAPDEC_CASE_BWDPS)
+        default: return cudaErrorNotSupported;
+    }
+}
+
 }  // namespace mdk

@@ -3,6 +3,7 @@
 
 #include "mapdec_kernels.h"
 #include "producers.cuh"
+#include "producers_ps.cuh"
 #include "producers_tc.cuh"
 
 namespace mdk {
@@ -64,6 +65,24 @@ cudaError_t launch_bwd_tc_t(const FrameDev *fr, const Work *w, int nw, size_t sm
     }
 }
 
+// Per-symbol-codebook producers (producers_ps.cuh).
+template <int NB, int IB>
+cudaError_t launch_fwd_ps_t(const FrameDev *fr, const Work *w, int nw, cudaStream_t st) {
+    if (nw <= 0) return cudaSuccess;
+    k_fwd_ps<NB, IB><<<nw, kThreads, 0, st>>>(fr, w);
+    return cudaGetLastError();
+}
+template <int NB, int IB, bool GRAD>
+cudaError_t launch_bwd_ps_t(const FrameDev *fr, const Work *w, int nw, size_t smem,
+                            cudaStream_t st) {
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_optin_once(k_bwd_ps<NB, IB, GRAD>, attr);
+    if (e != cudaSuccess) return e;
+    if (nw <= 0) return cudaSuccess;
+    k_bwd_ps<NB, IB, GRAD><<<nw, kThreads, smem, st>>>(fr, w);
+    return cudaGetLastError();
+}
+
 template <int NB, int IB>
 cudaError_t launch_rmetric_t(const FrameDev *fr, long long nthreads, cudaStream_t st) {
     if (nthreads <= 0) return cudaSuccess;
@@ -86,5 +105,7 @@ cudaError_t launch_rmetric_t(const FrameDev *fr, long long nthreads, cudaStream_
 #define MAPDEC_CASE_RM(NV) case NV: return launch_rmetric_t<NV, MAPDEC_IB>(frame, nthreads, st);
 #define MAPDEC_CASE_FWDTC(NV) case NV: return launch_fwd_tc_t<NV, MAPDEC_IB>(frames, work, nwork, smem, st);
 #define MAPDEC_CASE_BWDTC(NV) case NV: return launch_bwd_tc_t<NV, MAPDEC_IB>(frames, work, nwork, smem, st);
+#define MAPDEC_CASE_FWDPS(NV) case NV: return launch_fwd_ps_t<NV, MAPDEC_IB>(frames, work, nwork, st);
+#define MAPDEC_CASE_BWDPS(NV) case NV: return launch_bwd_ps_t<NV, MAPDEC_IB, grad>(frames, work, nwork, smem, st);
 #define MAPDEC_FOR_N_TC(M) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)
 #define MAPDEC_FOR_N(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)

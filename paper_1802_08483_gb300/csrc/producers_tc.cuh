@@ -1,24 +1,13 @@
-// Tensor-core forward producer (tcgen05): the same work as k_fwd -- lattices
-// of a tile of Pf received positions (eqs. F / F_lastrow) and the prior-weighted
-// transition sums W_i(s', j) = sum_D prior_i(D) R[n i + s' - xmax][D][j] (eq.
-// gamma summed over D) -- with the contraction over D on the tensor cores.
-//
-// Per tile the contraction is the dense product
-//     C[k][il] = sum_D R[k][D] prior[ilo + il][D],   k = pl * MN + j,
-// M = the tile's Pf * MN (position, length) rows in 128-row tiles, N = the
-// tile's symbols (a multiple of 16, at most 256), K = q (a multiple of 16).
-// FP32 accuracy from bf16 operands: each operand x is split as x = hi + lo
-// (hi = bf16(x), lo = bf16(x - hi)) and C = Rhi Phi + Rhi Plo + Rlo Phi, three
-// MMAs accumulating in FP32 in tensor memory; the dropped Rlo Plo term and the
-// rounding of lo are about 2^-16 of each product.
-//
-// Shared memory: Rhi, Rlo [MT*128 rows][q] and Phi, Plo [NN rows][q], bf16,
-// K-major (layout in tcgen05.cuh).  Rows beyond the tile's data are never
-// written: they only feed output rows / columns that are not stored.
-// Tensor memory: 256 columns, two accumulators of 128 columns when NN <= 128
-// (the MMAs of M-tile t+1 overlap the epilogue of M-tile t), else one.
-// Every CTA that allocates tensor memory frees it before it exits; the waits
-// on MMA completion are bounded (ST_TIMEOUT).
+// Tensor-core producers (tcgen05).  FP32 accuracy from bf16 operands: an
+// operand x is split into bf16 pieces, x = x0 + x1 (+ x2), x_k = bf16 of what
+// the earlier pieces left, rounded to nearest, and the product is the sum of
+// the piece products of low order, accumulated in FP32 in tensor memory.
+//   three pieces, six products (x0 y0, x0 y1, x1 y0, x0 y2, x1 y1, x2 y0): the
+//     dropped terms and the representation error are about 2^-24 of each
+//     product -- the W contraction, whose errors the recursions carry along
+//     the frame;
+//   two pieces, three products: about 2^-16 -- the APP contraction, whose
+//     error enters each symbol's APP once.
 #pragma once
 
 #include "mapdec_kernels.h"
@@ -27,19 +16,68 @@
 
 namespace mdk {
 
-constexpr int kTcCols = 256;  // tensor-memory columns per CTA (two CTAs per SM)
+constexpr int kTcCols = 256;  // tensor-memory columns per forward CTA (two CTAs per SM)
 constexpr uint32_t kTcWaitLimit = 1u << 26;
 
 __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
     return mbar_wait(bar, parity, kTcWaitLimit);
 }
 
+// Two floats rounded to bf16 and packed: a in the low half, b in the high half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&t);
+}
+
+// 8 consecutive values split into three bf16 pieces, each packed as 8 bf16
+// (16 bytes, element e at bits 16 (e % 2) of word e / 2).
+__device__ __forceinline__ void split3_x8(const float (&v)[8], uint4 &p0, uint4 &p1, uint4 &p2) {
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float a = v[2 * e], b = v[2 * e + 1];
+        uint32_t h = pack_bf16x2(a, b);
+        a -= __uint_as_float(h << 16);
+        b -= __uint_as_float(h & 0xffff0000u);
+        uint32_t m = pack_bf16x2(a, b);
+        a -= __uint_as_float(m << 16);
+        b -= __uint_as_float(m & 0xffff0000u);
+        w0[e] = h;
+        w1[e] = m;
+        w2[e] = pack_bf16x2(a, b);
+    }
+    p0 = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    p1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    p2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core forward producer: the same work as k_fwd -- the lattices of a
+// tile of Pf received positions (eqs. F / F_lastrow) and the prior-weighted
+// transition sums W_i(s', j) = sum_D prior_i(D) R[n i + s' - xmax][D][j] (eq.
+// gamma summed over D) -- with the contraction over D on the tensor cores:
+//     C[m][c] = sum_D R[m][D] prior[ilo8 + c][D],   m = pl * MNp + j,
+// MNp = MN rounded up to 8 (rows j >= MN of a position are padding), M = the
+// tile's Pf * MNp rows in 128-row tiles, N = NNa symbols starting at the
+// 8-aligned ilo8 <= ilo (a multiple of 16, at most 256), K = q.  Three
+// pieces, six products.
+// Shared memory: R, 3 pieces, MN-major (M contiguous in the 16-byte rows of a
+// core matrix: byte(m, D) = (D / 8) (MT 128 / 8) 128 + (m / 8) 128 + (D % 8) 16
+// + (m % 8) 2), so a lattice thread stores 8 consecutive lengths j as one
+// 16-byte vector per piece; then the priors block, bulk-copied from f.Pbuf
+// during the lattices.  Rows that hold no data only feed outputs that are not
+// stored.  Tensor memory: 256 columns, two accumulators of 128 when NNa <= 128
+// (the next M-tile's MMAs overlap this one's epilogue), else one.  Every CTA
+// that allocates tensor memory frees it before it exits; every wait is
+// bounded (ST_TIMEOUT).
+// ---------------------------------------------------------------------------
 template <int NB, int IB>
 __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restrict__ frames,
                                                         const Work *__restrict__ work) {
     static_assert(NB > 0, "compile-time lattice only");
     constexpr int n = NB;
     constexpr int MN = NB * (IB + 1) + 1;
+    constexpr int MNp = (MN + 7) & ~7;
     const Work wk = work[blockIdx.x];
     const FrameDev &f = frames[wk.frame];
     const int q = f.q, P = f.Pf, M = f.M, xmax = f.xmax;
@@ -47,41 +85,44 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restri
     const long long p0 = (long long)wk.tile * P;
     int ilo, ihi;
     tile_symbols(f, wk.tile, ilo, ihi);
-    const int S = ihi - ilo + 1;
-    if (S <= 0) return;  // uniform over the CTA, before any tensor memory is held
-    const int NC = P * MN;
-    const int MT = (NC + 127) >> 7;
-    const int NN = (S + 15) & ~15;
+    if (ihi < ilo) return;  // uniform over the CTA, before any tensor memory is held
+    const int ilo8 = ilo & ~7;
+    const int NNa = (ihi - ilo8 + 1 + 15) & ~15;
+    const int NR = P * MNp;
+    const int MT = (NR + 127) >> 7;
+    const int mg = MT * 16;  // 8-row groups of the R operand
     const int kc = q >> 3;
-    const int nbuf = NN <= 128 ? 2 : 1;
+    const int nbuf = NNa <= 128 ? 2 : 1;
+    const uint32_t pbytes = (uint32_t)(NNa >> 3) * 3u * (uint32_t)kc * 128u;
 
     extern __shared__ __align__(128) unsigned char tsm[];
-    unsigned char *Rhi = tsm;
-    unsigned char *Rlo = Rhi + (size_t)MT * 128 * q * 2;
-    unsigned char *Phi = Rlo + (size_t)MT * 128 * q * 2;
-    unsigned char *Plo = Phi + (size_t)NN * q * 2;
+    unsigned char *R0 = tsm;  // piece k at R0 + k * MT 128 q 2
+    const size_t rpiece = (size_t)MT * 128 * q * 2;
+    unsigned char *Pb = R0 + 3 * rpiece;
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_bar[3];  // [0], [1]: MMA accumulators; [2]: priors copy
     __shared__ int s_fail;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(&s_tmem, kTcCols);
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
+        for (int b = 0; b < 3; ++b) mbar_init(&s_bar[b], 1);
         fence_mbar_init();
+        // the tile's priors block: groups ilo8/8 .. ilo8/8 + NNa/8 - 1 of f.Pbuf
+        mbar_expect_tx(&s_bar[2], pbytes);
+        bulk_g2s(Pb, f.Pbuf + (size_t)(ilo8 >> 3) * 3 * kc * 128, pbytes, &s_bar[2]);
     }
 
-    // (A) lattices: a warp covers 4 positions x 8 codewords (conflict-free
-    // stores: MN is odd, so the 4 rows land in distinct 16-byte row slots)
+    // (A) lattices: a warp covers 4 positions x 8 codewords; a quarter warp
+    // (one position, 8 codewords) stores 128 contiguous bytes per chunk
     const int nblk = ((P + 3) >> 2) * (q >> 3);
     for (int b = warp; b < nblk; b += kThreads / 32) {
         const int pb = b / (q >> 3), db = b - pb * (q >> 3);
         const int pl = pb * 4 + (lane >> 3), D = db * 8 + (lane & 7);
         if (pl >= P) continue;
         const long long p = p0 + pl;
-        float v[kMaxMN];
+        float v[MNp];
         if (p <= rho) {
             eval_metric<NB, IB, 0>(f, p, D, v);
         } else {
@@ -89,71 +130,80 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restri
             for (int j = 0; j < MN; ++j) v[j] = 0.f;
         }
 #pragma unroll
-        for (int j = 0; j < MN; ++j) {
-            __nv_bfloat16 h, l;
-            tc::split_bf16(v[j], h, l);
-            const uint32_t o = tc::op_offset(pl * MN + j, D, kc);
-            *reinterpret_cast<__nv_bfloat16 *>(Rhi + o) = h;
-            *reinterpret_cast<__nv_bfloat16 *>(Rlo + o) = l;
+        for (int j = MN; j < MNp; ++j) v[j] = 0.f;
+        const uint32_t dbase = (uint32_t)(D >> 3) * (uint32_t)mg * 128u + (uint32_t)(D & 7) * 16u;
+#pragma unroll
+        for (int c = 0; c < MNp / 8; ++c) {
+            float x[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = v[c * 8 + e];
+            uint4 a0, a1, a2;
+            split3_x8(x, a0, a1, a2);
+            const uint32_t o = dbase + (uint32_t)((pl * MNp + c * 8) >> 3) * 128u;
+            *reinterpret_cast<uint4 *>(R0 + o) = a0;
+            *reinterpret_cast<uint4 *>(R0 + rpiece + o) = a1;
+            *reinterpret_cast<uint4 *>(R0 + 2 * rpiece + o) = a2;
         }
-    }
-    // (B) priors of the touched symbols, rows il < S
-    for (int e = tid; e < S * q; e += kThreads) {
-        const int il = e / q, D = e - il * q;
-        __nv_bfloat16 h, l;
-        tc::split_bf16(__ldg(f.priors + (size_t)(ilo + il) * q + D), h, l);
-        const uint32_t o = tc::op_offset(il, D, kc);
-        *reinterpret_cast<__nv_bfloat16 *>(Phi + o) = h;
-        *reinterpret_cast<__nv_bfloat16 *>(Plo + o) = l;
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = tc::idesc_bf16(128, NN);
+    const uint32_t idesc = tc::idesc_bf16(128, NNa) | (1u << 15);  // A MN-major
 
     // MMAs of M-tile t into accumulator t % nbuf (one thread)
     auto issue = [&](int t) {
         const uint32_t d = tmem + (uint32_t)((t % nbuf) * 128);
-        const uint32_t aoff = (uint32_t)t * 16u * (uint32_t)kc * 128u;  // 128 rows = 16 groups
-        const uint32_t ah = smem_u32(Rhi) + aoff, al = smem_u32(Rlo) + aoff;
-        const uint32_t bh = smem_u32(Phi), bl = smem_u32(Plo);
+        const uint32_t rb = smem_u32(R0) + (uint32_t)t * 16u * 128u;
+        const uint32_t pbs = smem_u32(Pb);
+        const int pa[6] = {0, 0, 1, 0, 1, 2}, pp[6] = {0, 1, 0, 2, 1, 0};
         for (int k0 = 0; k0 < q; k0 += 16) {
-            const uint32_t ko = (uint32_t)(k0 >> 3) * 128u;
-            tc::mma_bf16(d, tc::smem_desc(ah + ko, kc), tc::smem_desc(bh + ko, kc), idesc,
-                         k0 > 0 ? 1u : 0u);
-            tc::mma_bf16(d, tc::smem_desc(ah + ko, kc), tc::smem_desc(bl + ko, kc), idesc, 1u);
-            tc::mma_bf16(d, tc::smem_desc(al + ko, kc), tc::smem_desc(bh + ko, kc), idesc, 1u);
+#pragma unroll
+            for (int pr = 0; pr < 6; ++pr) {
+                const uint32_t a = rb + (uint32_t)pa[pr] * (uint32_t)rpiece +
+                                   (uint32_t)(k0 >> 3) * (uint32_t)mg * 128u;
+                const uint32_t bsm = pbs + (uint32_t)pp[pr] * (uint32_t)kc * 128u +
+                                     (uint32_t)(k0 >> 3) * 128u;
+                const uint64_t da = tc::smem_desc_mn(a, (uint32_t)mg);
+                const uint64_t db = tc::smem_desc_kmajor(bsm, 3u * (uint32_t)kc);
+                tc::mma_bf16(d, da, db, idesc, (k0 > 0 || pr > 0) ? 1u : 0u);
+            }
         }
         tc::commit(&s_bar[t % nbuf]);
     };
-    if (tid == 0)
-        for (int t = 0; t < nbuf && t < MT; ++t) issue(t);
+    if (tid == 0) {
+        if (!tc_wait(&s_bar[2], 0)) s_fail = ST_TIMEOUT;  // the priors block has landed
+        tc::fence_after_sync();
+        if (!s_fail)
+            for (int t = 0; t < nbuf && t < MT; ++t) issue(t);
+    }
+    __syncthreads();
+    const bool issued = !s_fail;
 
-    // (C) epilogue per M-tile: TMEM lane = row k of the tile, 16 columns per load;
-    // the two warpgroups take alternate 16-column chunks.  For one symbol, 32
-    // consecutive rows k are 32 consecutive floats of W (MNS == MN).
+    // (C) epilogue per M-tile: TMEM lane = row m of the tile, 16 columns per
+    // load; the two warpgroups take alternate 16-column chunks.  For one symbol
+    // the valid rows of a warp are runs of consecutive floats of W (MNS == MN).
     const int lg = warp & 3, half = warp >> 2;
-    for (int t = 0; t < MT; ++t) {
+    for (int t = 0; t < MT && issued; ++t) {
         const int buf = t % nbuf;
         if (!tc_wait(&s_bar[buf], (uint32_t)((t / nbuf) & 1))) s_fail = ST_TIMEOUT;
         tc::fence_after_sync();
-        const int k = t * 128 + lg * 32 + lane;
-        const int pl = k / MN, j = k - pl * MN;
+        const int m = t * 128 + lg * 32 + lane;
+        const int pl = m / MNp, j = m - pl * MNp;
         const long long p = p0 + pl;
-        const bool rowok = k < NC && p <= rho && !s_fail;
-        const long long sbase = p - (long long)n * ilo + xmax;  // drift state for il = 0
+        const bool rowok = pl < P && j < MN && p <= rho && !s_fail;
+        const long long sbase = p - (long long)n * ilo8 + xmax;  // drift state for c = 0
         const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * 128);
-        for (int c0 = half * 16; c0 < NN; c0 += 32) {
+        for (int c0 = half * 16; c0 < NNa; c0 += 32) {
             float v[16];
             tc::ld16(ta + (uint32_t)c0, v);
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                const int il = c0 + e;
-                const long long s = sbase - (long long)n * il;
-                if (rowok && il < S && s >= 0 && s < M)
-                    f.W[(size_t)(ilo + il) * f.wblk + s * f.MNS + j] = v[e];
+                const int i = ilo8 + c0 + e;
+                const long long s = sbase - (long long)n * (c0 + e);
+                if (rowok && i >= ilo && i <= ihi && s >= 0 && s < M)
+                    f.W[(size_t)i * f.wblk + s * f.MNS + j] = v[e];
             }
         }
         tc::fence_before_sync();

@@ -27,18 +27,36 @@ __host__ __device__ constexpr uint32_t op_offset(int r, int k, int kc) {
     return (uint32_t)((r >> 3) * kc * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// Shared-memory matrix descriptor: start address, LBO = 128, SBO = kc * 128,
-// descriptor version 1, no swizzle, base offset 0.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t kc) {
+// Shared-memory matrix descriptor: start address, leading- and stride-
+// dimension byte offsets, descriptor version 1, no swizzle, base offset 0.
+__device__ __forceinline__ uint64_t smem_desc_raw(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(((kc * 128u) >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
+// K-major operand as above: LBO = 128 between K chunks, SBO = group_chunks * 128
+// between 8-row groups (group_chunks = kc for one piece, or the chunks of all
+// pieces stored in one 8-row group).
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t group_chunks) {
+    return smem_desc_raw(saddr, 128u, group_chunks * 128u);
+}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t kc) {
+    return smem_desc_kmajor(saddr, kc);
+}
+// MN-major operand (M contiguous inside the 16-byte rows of a core matrix, the
+// rows of a core matrix 8 consecutive K): for this major-ness the leading-
+// dimension byte offset is the stride between 8-deep K groups (mg * 128 here,
+// mg = 8-element M groups of the operand) and the stride-dimension byte
+// offset the stride between 8-element M groups (128 here).
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr, uint32_t mg) {
+    return smem_desc_raw(saddr, mg * 128u, 128u);
+}
 
-// Instruction descriptor of kind::f16: bf16 A and B (both K-major), FP32
-// accumulator, M x N (M = 128; N a multiple of 16 up to 256).
+// Instruction descriptor of kind::f16: bf16 A and B (both K-major; bit 15
+// set makes A MN-major), FP32 accumulator, M x N (M = 128; N a multiple of 16
+// up to 256).
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);

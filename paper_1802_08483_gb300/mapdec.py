@@ -49,7 +49,8 @@ class FrameDesc(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int), ("n", ctypes.c_int), ("N", ctypes.c_int),
                 ("I", ctypes.c_int), ("xmax", ctypes.c_int), ("Pi", ctypes.c_double),
                 ("Pd", ctypes.c_double), ("Ps", ctypes.c_double),
-                ("codebook", ctypes.c_void_p), ("rx_len", ctypes.c_int64)]
+                ("codebook", ctypes.c_void_p), ("rx_len", ctypes.c_int64),
+                ("codebook_per_symbol", ctypes.c_int)]
 
 
 _lib = None
@@ -83,7 +84,7 @@ _SIGS = {
     "mapdec_batch_last_launches": (ctypes.c_int64, [_VP]),
     "mapdec_batch_phase_ms": (ctypes.c_int, [_VP, _VP]),
     "mapdec_batch_num_waves": (ctypes.c_int, [_VP]),
-    "mapdec_batch_tc_frames": (ctypes.c_int, [_VP]),
+    "mapdec_batch_tc_frames": (ctypes.c_int, [_VP, _VP]),
     "mapdec_fp32_fma_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _VP]),
     "mapdec_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
     "mapdec_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
@@ -213,8 +214,10 @@ def mapdec_batch_create(frames, flags=0, mem_budget_bytes=0):
         cb = np.ascontiguousarray(fr.codebook, dtype=np.uint8)
         keep.append(cb)
         rho = fr.rho if hasattr(fr, "rho") else int(fr.rx_len)
+        # a (q, n) codebook serves every symbol; (N, q, n) gives one per symbol
         arr[k] = FrameDesc(int(fr.q), int(fr.n), int(fr.N), int(fr.I), int(fr.xmax),
-                           float(fr.Pi), float(fr.Pd), float(fr.Ps), cb.ctypes.data, int(rho))
+                           float(fr.Pi), float(fr.Pd), float(fr.Ps), cb.ctypes.data, int(rho),
+                           1 if cb.ndim == 3 else 0)
     b = _VP()
     _check(lib.mapdec_batch_create(ctypes.byref(b), arr, len(frames), int(flags),
                                    int(mem_budget_bytes)), "mapdec_batch_create")
@@ -293,8 +296,14 @@ def mapdec_batch_num_waves(b):
     return int(load().mapdec_batch_num_waves(b))
 
 
-def mapdec_batch_tc_frames(b):
-    return int(load().mapdec_batch_tc_frames(b))
+def mapdec_batch_tc_frames(b, nframes=None):
+    """Frames whose forward producer runs on the tensor cores; with nframes,
+    (count, per-frame flags: bit 0 forward producer, bit 1 APP producer)."""
+    if nframes is None:
+        return int(load().mapdec_batch_tc_frames(b, None))
+    fl = np.zeros(int(nframes), np.int32)
+    c = int(load().mapdec_batch_tc_frames(b, _ptr(fl)))
+    return c, fl
 
 
 def mapdec_tune_set(q, n, I, tune=None):

@@ -50,7 +50,7 @@ class Frame:
     Pi: float
     Pd: float
     Ps: float
-    codebook: np.ndarray          # (q, n) uint8 0/1, distinct rows
+    codebook: np.ndarray          # (q, n) uint8 0/1, distinct rows; or (N, q, n): one per symbol
     message: np.ndarray           # (N,) int64
     priors: Optional[np.ndarray]  # (N, q) float32, or None for uniform
     rx: np.ndarray                # (rho,) uint8 0/1
@@ -134,6 +134,24 @@ def make_frame(rng: np.random.Generator, q: int, n: int, N: int, I: int, xmax: i
         raise RuntimeError("could not draw a realisation within the drift limit")
     return Frame(q=q, n=n, N=N, I=I, xmax=xmax, Pi=float(Pi), Pd=float(Pd), Ps=float(Ps),
                  codebook=codebook, message=msg.astype(np.int64), priors=priors, rx=rx, tag=tag)
+
+
+def per_symbol_frame(rng: np.random.Generator, q: int, n: int, N: int, I: int, xmax: int,
+                     Pi: float, Pd: float, Ps: float, tag: str = "") -> Frame:
+    """Frame whose symbol i is sent with its own random codebook C_i (an (N, q, n)
+    codebook array), Dirichlet(1) priors, message drawn from the priors."""
+    books = np.stack([random_codebook(rng, q, n) for _ in range(N)])
+    priors = dirichlet_priors(rng, N, q)
+    msg = draw_message(rng, priors, N, q)
+    x = books[np.arange(N), msg].reshape(-1)
+    for _ in range(10000):
+        rx = bsid_channel(rng, x, Pi, Pd, Ps, I)
+        if abs(rx.size - x.size) <= xmax:
+            break
+    else:
+        raise RuntimeError("could not draw a realisation within the drift limit")
+    return Frame(q=q, n=n, N=N, I=I, xmax=xmax, Pi=float(Pi), Pd=float(Pd), Ps=float(Ps),
+                 codebook=books, message=msg.astype(np.int64), priors=priors, rx=rx, tag=tag)
 
 
 def c3_params(rng: np.random.Generator):

@@ -70,3 +70,18 @@ def test_phase_traffic_follows_the_source_hash(tmp_path):
     assert bench.phase_traffic("backward", str(good)) == 123
     assert bench.phase_traffic("backward", str(stale)) is None
     assert bench.phase_traffic("backward", str(tmp_path / "missing.json")) is None
+
+
+def test_pipe_flops_split():
+    """The per-pipe split moves exactly the contractions of tensor-core frames
+    to the tensor pipe; the sum over pipes is the algorithmic total."""
+    fr = synth.config_frame(3, 5)
+    ff = bench.frame_flops(fr)
+    total = ff["forward"] + ff["chains"] + ff["backward"]
+    w = 2 * fr.q * ff["V"]
+    for bits in (0, 1, 3):
+        pf = bench.pipe_flops(fr, bits)
+        assert sum(pf[k]["fp32"] + pf[k]["tensor"] for k in pf) == total
+        assert pf["forward"]["tensor"] == (w if bits & 1 else 0)
+        assert pf["backward"]["tensor"] == (w if bits & 2 else 0)
+        assert pf["backward"]["executed_fp32"] == pf["backward"]["fp32"] + ff["lattice"]

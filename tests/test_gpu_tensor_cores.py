@@ -49,7 +49,7 @@ def _frames():
     return out
 
 
-def _decode(frames, monkeypatch=None, tc=None, tc_bwd=None):
+def _decode(frames, monkeypatch=None, tc="1", tc_bwd=None):
     if monkeypatch is not None and tc is not None:
         monkeypatch.setenv("MAPDEC_TC", tc)
     if monkeypatch is not None and tc_bwd is not None:
@@ -68,7 +68,7 @@ def _decode(frames, monkeypatch=None, tc=None, tc_bwd=None):
 def test_tensor_core_batch_against_oracle(monkeypatch, tc_bwd):
     """tc_bwd = 0: tensor cores in the forward producer only; 1: both producers."""
     frames = _frames()
-    ntc, apps, ll = _decode(frames, monkeypatch, None, tc_bwd)
+    ntc, apps, ll = _decode(frames, monkeypatch, "1", tc_bwd)
     assert ntc == len(frames) - 1, ntc  # all but case 308 (> 256 symbols per tile)
     for k, fr in enumerate(frames):
         app_ref, ll_ref = oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I, fr.xmax,
@@ -82,16 +82,16 @@ def test_tensor_cores_off_agrees(monkeypatch):
     frames = _frames()
     ntc0, apps0, ll0 = _decode(frames, monkeypatch, "0")
     assert ntc0 == 0
-    monkeypatch.delenv("MAPDEC_TC")
-    ntc1, apps1, ll1 = _decode(frames)
+    ntc1, apps1, ll1 = _decode(frames, monkeypatch, "1")
     assert ntc1 > 0
     for k in range(len(frames)):
         check_app(apps1[k], apps0[k], what=f"case {TC_CASES[k][0]}")
         check_ll(ll1[k], ll0[k], what=f"case {TC_CASES[k][0]}")
 
 
-def test_single_frame_handle_uses_tensor_cores():
+def test_single_frame_handle_uses_tensor_cores(monkeypatch):
     """The single-frame path (one frame per call) runs the same producers."""
+    monkeypatch.setenv("MAPDEC_TC", "1")
     fr = _frames()[3]
     dec = mapdec.Decoder.for_frame(fr)
     app, ll = dec.decode(fr.rx, fr.priors)
