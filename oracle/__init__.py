@@ -83,9 +83,9 @@ def _load():
         lib.orc_loglik_grad.argtypes = common + [ctypes.c_int, dp, dp, dp]
         lib.orc_loglik_grad.restype = ctypes.c_int
         general = common[:3] + [ctypes.c_int] + common[3:]
-        lib.orc_decode_general.argtypes = general + [ctypes.c_int, dp, dp, dp]
+        lib.orc_decode_general.argtypes = general + [ctypes.c_int, dp, dp, dp, dp, dp]
         lib.orc_decode_general.restype = ctypes.c_int
-        lib.orc_loglik_grad_general.argtypes = general + [ctypes.c_int, dp, dp, dp]
+        lib.orc_loglik_grad_general.argtypes = general + [ctypes.c_int, dp, dp, dp, dp, dp]
         lib.orc_loglik_grad_general.restype = ctypes.c_int
         lib.orc_set_received_bit_weight.argtypes = [ctypes.c_double]
         lib.orc_set_received_bit_weight.restype = None
@@ -205,12 +205,28 @@ def _general_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors):
     return q, n, args[:3] + [per_symbol] + args[3:], keep
 
 
-def decode_ext(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True, kappa=1.0):
+def _boundary(phi, xmax, keep):
+    """Drift prior over the 2 xmax + 1 boundary states (index m + xmax), or NULL."""
+    if phi is None:
+        return _NULL_D
+    a = np.ascontiguousarray(phi, np.float64).reshape(-1)
+    if a.size != 2 * xmax + 1:
+        raise ValueError(f"a boundary drift prior has 2 xmax + 1 = {2 * xmax + 1} entries")
+    keep.append(a)
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def decode_ext(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True, kappa=1.0,
+               drift_start=None, drift_end=None):
     """(APPs (N, q), extrinsic outputs (N, q), log P(Y)) of one frame (FP64).
 
     codebook is (q, n), one codebook for every symbol, or (N, q, n), the
     constituent encodings C_i of Sec. II-A.  The extrinsic output of symbol i
-    is eq. (L) without the symbol's own prior, normalised over D."""
+    is eq. (L) without the symbol's own prior, normalised over D.
+    drift_start / drift_end: priors of the drift at the frame's start and end
+    (2 xmax + 1 values, index m + xmax; the boundaries alpha_0, beta_N of
+    Sec. II-C in stream decoding), None for an isolated frame
+    (alpha_0 = [m = 0], beta_N = [m = rho - tau])."""
     lib = _load()
     lib.orc_set_received_bit_weight(float(kappa))
     q, n, args, keep = _general_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
@@ -219,16 +235,18 @@ def decode_ext(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True, kap
     ext = np.zeros((N, q), np.float64)
     ll = ctypes.c_double(0.0)
     st = lib.orc_decode_general(*args, int(bool(memo)), app.ctypes.data_as(dpp),
-                                ext.ctypes.data_as(dpp), ctypes.byref(ll))
+                                ext.ctypes.data_as(dpp), ctypes.byref(ll),
+                                _boundary(drift_start, xmax, keep), _boundary(drift_end, xmax, keep))
     if st:
         raise OracleError(st, "decode_ext")
     return app, ext, ll.value
 
 
 def loglik_grad(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True,
-                want_chan=True, want_priors=True, kappa=1.0):
+                want_chan=True, want_priors=True, kappa=1.0, drift_start=None, drift_end=None):
     """(logP, d logP/d(Pi,Pd,Ps) or None, d logP/d priors (N,q) or None).
-    codebook is (q, n) or per-symbol (N, q, n), as for decode_ext."""
+    codebook is (q, n) or per-symbol (N, q, n), and the boundary drift priors,
+    as for decode_ext."""
     lib = _load()
     lib.orc_set_received_bit_weight(float(kappa))
     q, n, args, keep = _general_args(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors)
@@ -239,7 +257,8 @@ def loglik_grad(codebook, N, Pi, Pd, Ps, I, xmax, rx, priors=None, memo=True,
     st = lib.orc_loglik_grad_general(*args, int(bool(memo)),
                                      dchan.ctypes.data_as(dpp) if want_chan else _NULL_D,
                                      dpri.ctypes.data_as(dpp) if want_priors else _NULL_D,
-                                     ctypes.byref(ll))
+                                     ctypes.byref(ll), _boundary(drift_start, xmax, keep),
+                                     _boundary(drift_end, xmax, keep))
     if st:
         raise OracleError(st, "loglik_grad")
     return ll.value, dchan, dpri

@@ -218,6 +218,8 @@ typedef struct {
     size_t cb_stride;   /* 0: C_i = C for every i; q*n: codebook C_i at cb + i*q*n */
     const uint8_t *rx;  /* rho received bits */
     const double *pri;  /* N*q priors, or NULL for uniform 1/q */
+    const double *phi0; /* M: prior of the drift at the frame start (alpha_0), or NULL: [m = 0] */
+    const double *phiN; /* M: prior of the drift at the frame end (beta_N), or NULL: [m = rho - tau] */
     int memo;
     double *Rm;         /* memo, (rho+1)*q*Mn, valid where Rk[p] set */
     uint8_t *Rk;
@@ -387,6 +389,71 @@ static void orc_free(orc_ctx *c)
 }
 
 /*
+ * Frame boundaries (Sec. II-C: alpha_0 and beta_N are the prior probabilities
+ * of the frame boundaries).  An isolated frame has alpha_0(m) = [m = 0] and
+ * beta_N(m) = [m = rho - tau].  In stream decoding the boundaries are
+ * uncertain and carry drift priors phi0, phiN: the frame starts at received
+ * position m0 with probability phi0(m0) (bits before it belong to the previous
+ * frame) and ends at tau + mN with probability phiN(mN) (bits after it belong
+ * to the next one), so
+ *   P(Y) = sum_{m0, mN} phi0(m0) P(Y[m0 .. tau + mN) | frame) phiN(mN).
+ * With the received-bit weight kappa every gamma carries kappa^{received
+ * length}; a path from m0 to mN then carries kappa^{tau + mN - m0}.  The start
+ * row is weighted kappa^{m0} and the end row kappa^{-(tau + mN)}, so every
+ * path's weight cancels exactly (kappa = 1 is the paper's recursion).
+ * orc_start_row writes the normalised alpha_0 and adds the log of its sum to
+ * *ls; orc_end_row writes beta_N (unnormalised weights); orc_end_logp returns
+ * log of sum_m alpha_N(m) beta_N(m) for the normalised alpha_N.
+ */
+static int orc_start_row(const orc_ctx *c, double *A, double *ls)
+{
+    const int M = c->M;
+    if (!c->phi0) {
+        for (int m = 0; m < M; ++m) A[m] = 0.0;
+        A[c->xmax] = 1.0;
+        return ORC_OK;
+    }
+    double s = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double v = c->phi0[m];
+        if (!(v >= 0.0)) return ORC_ERR_ARG;
+        A[m] = v * pow(g_kappa, (double)(m - c->xmax));
+        s += A[m];
+    }
+    if (!(s > 0.0)) return ORC_ERR_ZERO_PROB;
+    for (int m = 0; m < M; ++m) A[m] /= s;
+    *ls += log(s);
+    return ORC_OK;
+}
+
+/* beta_N(m) kappa^tau: the end row's weights without the common kappa^{-tau},
+ * which log P takes separately (it would underflow). */
+static int orc_end_row(const orc_ctx *c, double *bN)
+{
+    const int M = c->M;
+    const int64_t tau = (int64_t)c->n * c->N;
+    for (int m = 0; m < M; ++m) bN[m] = 0.0;
+    if (!c->phiN) {
+        bN[(int)(c->rho - tau) + c->xmax] = pow(g_kappa, -(double)(c->rho - tau));
+        return ORC_OK;
+    }
+    for (int m = 0; m < M; ++m) {
+        const double v = c->phiN[m];
+        if (!(v >= 0.0)) return ORC_ERR_ARG;
+        bN[m] = v * pow(g_kappa, -(double)(m - c->xmax));
+    }
+    return ORC_OK;
+}
+
+/* log sum_m alpha_N(m) beta_N(m), the end of log P (with -tau log kappa). */
+static double orc_end_logp(const orc_ctx *c, const double *aN, const double *bN)
+{
+    double s = 0.0;
+    for (int m = 0; m < c->M; ++m) s += aN[m] * bN[m];
+    return (s > 0.0 ? log(s) : -INFINITY) - (double)((int64_t)c->n * c->N) * log(g_kappa);
+}
+
+/*
  * Forward pass, eqs. (alpha_prenorm), (alpha_norm):
  *   alpha'_{i+1}(m) = sum_{m', D} alpha_i(m') gamma_i(m', m, D),
  *   c_{i+1} = sum_m alpha'_{i+1}(m),  alpha_{i+1} = alpha'_{i+1} / c_{i+1}.
@@ -397,9 +464,9 @@ static int orc_forward(orc_ctx *c, double *A, double *logsum)
     const int M = c->M, q = c->q, Mn = c->Mn, n = c->n;
     double *g = (double *)malloc((size_t)M * q * Mn * sizeof(double));
     if (!g) return ORC_ERR_NOMEM;
-    for (int m = 0; m < M; ++m) A[m] = 0.0;
-    A[c->xmax] = 1.0; /* alpha_0(m) = [m = 0] */
     double ls = 0.0;
+    int st0 = orc_start_row(c, A, &ls);
+    if (st0) { free(g); return st0; }
     for (int i = 0; i < c->N; ++i) {
         int st = orc_gamma(c, i, g, NULL);
         if (st) { free(g); return st; }
@@ -436,8 +503,14 @@ static int orc_backward(orc_ctx *c, double *B)
     double *g = (double *)malloc((size_t)M * q * Mn * sizeof(double));
     if (!g) return ORC_ERR_NOMEM;
     double *bN = B + (size_t)N * M;
-    for (int m = 0; m < M; ++m) bN[m] = 0.0;
-    bN[(int)(c->rho - (int64_t)n * N) + c->xmax] = 1.0;
+    int st0 = orc_end_row(c, bN);
+    if (st0) { free(g); return st0; }
+    {  /* normalised like every other row (its scale never enters log P) */
+        double ds = 0.0;
+        for (int m = 0; m < M; ++m) ds += bN[m];
+        if (!(ds > 0.0)) { free(g); return ORC_ERR_ZERO_PROB; }
+        for (int m = 0; m < M; ++m) bN[m] /= ds;
+    }
     for (int i = N - 1; i >= 0; --i) {
         int st = orc_gamma(c, i, g, NULL);
         if (st) { free(g); return st; }
@@ -532,12 +605,14 @@ static int orc_app(orc_ctx *c, const double *A, const double *B, double *app, do
 int orc_decode_general(int q, int n, const uint8_t *codebooks, int per_symbol, int N, double Pi,
                        double Pd, double Ps, int I, int xmax, const uint8_t *rx, int64_t rho,
                        const double *priors, int memo, double *app, double *ext,
-                       double *loglik)
+                       double *loglik, const double *phi0, const double *phiN)
 {
     orc_ctx c;
     int st = orc_init(&c, q, n, codebooks, per_symbol, N, Pi, Pd, Ps, I, xmax, rx, rho, priors,
                       memo, 0);
     if (st) { orc_free(&c); return st; }
+    c.phi0 = phi0;
+    c.phiN = phiN;
     const size_t rows = (size_t)(N + 1) * c.M;
     double *A = (double *)malloc(rows * sizeof(double));
     double *B = (double *)malloc(rows * sizeof(double));
@@ -545,9 +620,10 @@ int orc_decode_general(int q, int n, const uint8_t *codebooks, int per_symbol, i
     double ls = 0.0;
     st = orc_forward(&c, A, &ls);
     if (!st) {
-        const double aN = A[(size_t)N * c.M + (int)(rho - (int64_t)n * N) + xmax];
-        if (!(aN > 0.0)) st = ORC_ERR_ZERO_PROB;
-        else if (loglik) *loglik = ls + log(aN) - (double)rho * log(g_kappa);
+        st = orc_end_row(&c, B);  /* B is overwritten by the backward pass below */
+        const double le = st ? 0.0 : orc_end_logp(&c, A + (size_t)N * c.M, B);
+        if (!st && !isfinite(le)) st = ORC_ERR_ZERO_PROB;
+        else if (!st && loglik) *loglik = ls + le;
     }
     if (!st && (app || ext)) st = orc_backward(&c, B);
     if (!st && (app || ext)) st = orc_app(&c, A, B, app, ext, NULL);
@@ -571,7 +647,7 @@ int orc_decode(int q, int n, const uint8_t *codebook, int N, double Pi, double P
                double *app, double *loglik)
 {
     return orc_decode_general(q, n, codebook, 0, N, Pi, Pd, Ps, I, xmax, rx, rho, priors, memo,
-                              app, NULL, loglik);
+                              app, NULL, loglik, NULL, NULL);
 }
 
 /*
@@ -627,24 +703,31 @@ int orc_forward_backward(int q, int n, const uint8_t *codebook, int N, double Pi
 int orc_loglik_grad_general(int q, int n, const uint8_t *codebooks, int per_symbol, int N,
                             double Pi, double Pd, double Ps, int I, int xmax, const uint8_t *rx,
                             int64_t rho, const double *priors, int memo, double *dlogp_dchan,
-                            double *dlogp_dpriors, double *loglik)
+                            double *dlogp_dpriors, double *loglik, const double *phi0,
+                            const double *phiN)
 {
     orc_ctx c;
     int st = orc_init(&c, q, n, codebooks, per_symbol, N, Pi, Pd, Ps, I, xmax, rx, rho, priors,
                       memo, dlogp_dchan != NULL);
     if (st) { orc_free(&c); return st; }
+    c.phi0 = phi0;
+    c.phiN = phiN;
     const int M = c.M, Mn = c.Mn;
-    const int end = (int)(rho - (int64_t)n * N) + xmax;
+    double *bN = (double *)malloc((size_t)M * sizeof(double));
+    double *a0 = (double *)malloc((size_t)M * sizeof(double));
+    if (!bN || !a0) { free(bN); free(a0); orc_free(&c); return ORC_ERR_NOMEM; }
+    double ls0 = 0.0;  /* log of the start row's sum (independent of the channel) */
+    st = orc_start_row(&c, a0, &ls0);
+    if (!st) st = orc_end_row(&c, bN);
+    if (st) { free(bN); free(a0); orc_free(&c); return st; }
     if (dlogp_dchan) {
         dual *g = (dual *)malloc((size_t)M * q * Mn * sizeof(dual));
         dual *a = (dual *)malloc((size_t)M * sizeof(dual));
         dual *an = (dual *)malloc((size_t)M * sizeof(dual));
         if (!g || !a || !an) st = ORC_ERR_NOMEM;
-        dual ls = d_const(0.0);
-        if (!st) {
-            for (int m = 0; m < M; ++m) a[m] = d_const(0.0);
-            a[xmax] = d_const(1.0);
-        }
+        dual ls = d_const(ls0);
+        if (!st)
+            for (int m = 0; m < M; ++m) a[m] = d_const(a0[m]);
         for (int i = 0; !st && i < N; ++i) {
             st = orc_gamma_dual(&c, i, g);
             if (st) break;
@@ -664,15 +747,17 @@ int orc_loglik_grad_general(int q, int n, const uint8_t *codebooks, int per_symb
             ls = d_add(ls, d_log(cs));
         }
         if (!st) {
-            if (!(a[end].v > 0.0)) st = ORC_ERR_ZERO_PROB;
+            dual e = d_const(0.0);  /* sum_m alpha_N(m) beta_N(m) */
+            for (int m = 0; m < M; ++m) e = d_add(e, d_scale(a[m], bN[m]));
+            if (!(e.v > 0.0)) st = ORC_ERR_ZERO_PROB;
             else {
-                dual lp = d_add(ls, d_log(a[end]));
+                dual lp = d_add(ls, d_log(e));
                 for (int k = 0; k < 3; ++k) dlogp_dchan[k] = lp.d[k];
-                if (loglik) *loglik = lp.v - (double)rho * log(g_kappa);
+                if (loglik) *loglik = lp.v - (double)((int64_t)n * N) * log(g_kappa);
             }
         }
         free(g); free(a); free(an);
-        if (st) { orc_free(&c); return st; }
+        if (st) { free(bN); free(a0); orc_free(&c); return st; }
     }
     if (dlogp_dpriors || (!dlogp_dchan && loglik)) {
         const size_t rows = (size_t)(N + 1) * M;
@@ -683,9 +768,9 @@ int orc_loglik_grad_general(int q, int n, const uint8_t *codebooks, int per_symb
         double ls = 0.0;
         if (!st) st = orc_forward(&c, A, &ls);
         if (!st && !dlogp_dchan && loglik) {
-            const double aN = A[(size_t)N * M + end];
-            if (!(aN > 0.0)) st = ORC_ERR_ZERO_PROB;
-            else *loglik = ls + log(aN) - (double)rho * log(g_kappa);
+            const double le = orc_end_logp(&c, A + (size_t)N * M, bN);
+            if (!isfinite(le)) st = ORC_ERR_ZERO_PROB;
+            else *loglik = ls + le;
         }
         if (!st && dlogp_dpriors) st = orc_backward(&c, B);
         if (!st && dlogp_dpriors) st = orc_app(&c, A, B, NULL, dlogp_dpriors, Z);
@@ -694,6 +779,7 @@ int orc_loglik_grad_general(int q, int n, const uint8_t *codebooks, int per_symb
                 for (int D = 0; D < q; ++D) dlogp_dpriors[(size_t)i * q + D] /= Z[i];
         free(A); free(B); free(Z);
     }
+    free(bN); free(a0);
     orc_free(&c);
     return st;
 }
@@ -705,5 +791,5 @@ int orc_loglik_grad(int q, int n, const uint8_t *codebook, int N, double Pi, dou
                     double *loglik)
 {
     return orc_loglik_grad_general(q, n, codebook, 0, N, Pi, Pd, Ps, I, xmax, rx, rho, priors,
-                                   memo, dlogp_dchan, dlogp_dpriors, loglik);
+                                   memo, dlogp_dchan, dlogp_dpriors, loglik, NULL, NULL);
 }
