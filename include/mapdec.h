@@ -128,6 +128,17 @@ int mapdec_loglik_grad(mapdec_t *h, const uint8_t *rx, int64_t rx_len, const flo
  */
 int mapdec_receiver_metric(mapdec_t *h, const uint8_t *rx, int64_t rx_len, float *R_out);
 
+/*
+ * Stream decoding with a single-frame handle: set (or, with NULL, clear) the
+ * drift priors of the frame's start and end (2*xmax+1 floats each, host or
+ * device; see mapdec_frame_desc_t.drift_start / drift_end) used by the
+ * following mapdec_decode, mapdec_decode_ext and mapdec_loglik_grad calls.
+ * The values are copied into buffers the handle allocated at create; nothing
+ * is allocated.  MAPDEC_ERR_ARG for negative or non-finite entries or an
+ * all-zero prior.
+ */
+int mapdec_set_drift_priors(mapdec_t *h, const float *drift_start, const float *drift_end);
+
 /* Release a handle and its device scratch (NULL is ignored). */
 void mapdec_destroy(mapdec_t *h);
 
@@ -155,6 +166,21 @@ typedef struct {
                                 work of one codebook.  Not with
                                 MAPDEC_BATCH_SEGMENTED or mapdec_decode_noalloc
                                 (MAPDEC_ERR_UNSUPPORTED). */
+    const float *drift_start;  /* stream decoding (Sec. II-C: alpha_0 and beta_N are the
+                                  priors of the frame boundaries): 2*xmax+1 floats, entry
+                                  m + xmax = Pr{the frame starts at received position m},
+                                  host or device, copied at create; NULL: the frame
+                                  starts at position 0 (alpha_0 = [m = 0]).  Mass at
+                                  m < 0 carries no path (no received bits there). */
+    const float *drift_end;    /* 2*xmax+1 floats, entry m + xmax = Pr{the frame ends
+                                  at received position tau + m}; received bits after
+                                  the end belong to the next frame.  NULL: the frame
+                                  ends at rx_len (beta_N = [m = rx_len - tau]).  With
+                                  boundary priors log P(Y) = log sum over both
+                                  boundaries of prior x likelihood of the piece between
+                                  them, and the APPs are the matching mixture.
+                                  Entries >= 0, finite, some positive; else
+                                  MAPDEC_ERR_ARG.  Not with mapdec_decode_noalloc. */
 } mapdec_frame_desc_t;
 
 /*
@@ -332,9 +358,11 @@ typedef struct {
                             forward and APP producers (decode only; about
                             (rho+1) * roundup4(q) * (n(I+1)+1) * 4 bytes per frame);
                             0 or -1: recompute them */
-    int tensor_cores;    /* 0 or 1: producers on the tensor cores where the class
-                            supports them (see mapdec_batch_tc_frames); 2: FP32
-                            CUDA-core producers */
+    int tensor_cores;    /* 0: the planner's rule (the forward producer on the tensor
+                            cores for frames whose tiles span at least 48 symbols,
+                            the APP producer on the CUDA cores); 1: both producers on
+                            the tensor cores wherever the class supports them (see
+                            mapdec_batch_tc_frames); 2: FP32 CUDA-core producers */
     int chain_threads;   /* block size of the recursion kernel: 128, 256 or 512
                             (0 = 256); the batch takes the value of its last frame
                             whose class sets it */
@@ -353,12 +381,14 @@ int mapdec_batch_num_waves(mapdec_batch_t *b);
 /*
  * Frames whose contractions run on the tensor cores (tcgen05, bf16 operands
  * split into high and low parts, FP32 accumulation; an implementation choice,
- * not in the paper).  The planner picks them in decode batches for classes
- * with q a multiple of 16 up to 64 and n >= 4 whose tiles fit (the other
- * frames, and every frame of a MAPDEC_BATCH_GRAD batch, use the FP32 CUDA-core
- * producers); the environment variables MAPDEC_TC=0 and MAPDEC_TC_BWD=0, read
- * when a batch is created, keep every frame's producers, or its APP producer,
- * on the CUDA cores.  If flags is not NULL it receives one int per frame: bit 0
+ * not in the paper).  The planner picks the forward producer's for decode
+ * batches, classes with q a multiple of 16 up to 64 and n >= 4 whose tiles fit
+ * and span at least 48 symbols (MAPDEC_TC_MIN_S overrides the count); the
+ * other frames, and every frame of a MAPDEC_BATCH_GRAD batch, use the FP32
+ * CUDA-core producers.  The environment variables, read when a batch is
+ * created: MAPDEC_TC=0 keeps every producer on the CUDA cores, MAPDEC_TC=1
+ * puts both producers on the tensor cores wherever supported, MAPDEC_TC_BWD
+ * switches the APP producer's choice on (1) or off (0).  If flags is not NULL it receives one int per frame: bit 0
  * set when the forward producer (W contraction) runs on the tensor cores,
  * bit 1 when the APP producer does.  Returns the number of frames with bit 0
  * set, or -1 for a NULL batch.

@@ -171,6 +171,47 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
         fence_mbar_init();
     }
     __syncthreads();
+    // Stream decoding: a boundary drift prior replaces the point mass
+    // (alpha_0 = phi0, beta_N = phiN; Sec. II-C).  In the tilted rows the start
+    // row is alpha^_0(m) = phi0(m) 2^m / Z_0 (tilt 1, received length m) and the
+    // end row beta^_N(m) is proportional to phiN(m) 2^-m; both are first scaled
+    // by 2^-emax (emax the largest exponent over the prior's support, exact),
+    // then divided by the power of two below their sum like every row, and
+    // log2 Z_0 = emax + that exponent starts the forward record.
+    const float *prior = !fresh ? nullptr : (dir == 0 ? f.phi0 : f.phiN);
+    __shared__ int s_emax;
+    long long zexp0 = 0;  // log2 Z_0 of a prior start row (forward)
+    float mean0 = (dir == 0) ? 0.f : (float)(send - xmax);
+    if (prior) {
+        if (threadIdx.x == 0) s_emax = -(1 << 30);
+        __syncthreads();
+        for (int s = threadIdx.x; s < M; s += blockDim.x)
+            if (prior[s] > 0.f) atomicMax(&s_emax, dir == 0 ? s - xmax : xmax - s);
+        __syncthreads();
+        const int emax = s_emax;
+        float part0 = 0.f, partm0 = 0.f;
+        for (int s = threadIdx.x; s < M; s += blockDim.x) {
+            const float w = prior[s];
+            const int e = (dir == 0 ? s - xmax : xmax - s) - emax;  // <= 0
+            const float v = (w > 0.f && e > -150) ? ldexpf(w, e) : 0.f;
+            cur[s] = v;
+            part0 += v;
+            partm0 = fmaf(v, (float)(s - xmax), partm0);
+        }
+        float c0, cm0;
+        block_sum2(part0, partm0, c0, cm0, red);
+        if (!(c0 > 0.f)) {  // no mass inside the drift limits (same in every thread)
+            if (threadIdx.x == 0) atomicMax(f.status, ST_ZERO);
+            return;         // nothing issued yet
+        }
+        int ex;
+        frexpf(c0, &ex);
+        const float inv = ldexpf(1.f, 1 - ex);
+        for (int s = threadIdx.x; s < M; s += blockDim.x) cur[s] *= inv;
+        zexp0 = (long long)emax + ex - 1;
+        mean0 = cm0 / c0;
+        __syncthreads();
+    }
     {
         float *row0 = (dir == 0) ? f.alpha + (size_t)i0 * Mp : f.beta + (size_t)i1 * Mp;
         for (int s = threadIdx.x; s < Mp; s += blockDim.x) row0[s] = cur[s];
@@ -215,10 +256,10 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
 
     // controller state (thread 0); log2 Z as an integer sum of the row
     // scalings plus the FP64 sum of the tilt terms (changed rows only)
-    long long zexp = 0;
+    long long zexp = zexp0;
     double ztilt = 0.0;
-    float theta = 1.f;                                    // tilt of the current row
-    float mean = (dir == 0) ? 0.f : (float)(send - xmax);  // its mean drift
+    float theta = 1.f;   // tilt of the current row
+    float mean = mean0;  // its mean drift
     float lrow = 0.f;      // log2 of the current row's sum
     float lc_prev = 0.f;   // sum of log2 growth since the last tilt update
     int lc_cnt = 0;        // number of steps in lc_prev
@@ -237,7 +278,7 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
     }
     if (replay) steps = i0;
     if (threadIdx.x == 0 && fresh && !replay) {
-        if (dir == 0) { f.thf[0] = 1.0; f.mcf[0] = 0.0; }
+        if (dir == 0) { f.thf[0] = 1.0; f.mcf[0] = (double)mean0; }
         else f.thb[N] = 1.0;
     }
     // this thread's share of the row sum and of its first moment
@@ -454,12 +495,35 @@ __global__ void __launch_bounds__(kChainMaxThreads) k_chain(const FrameDev *__re
         }
     }
     if (dir == 0 && !replay && i1 == N && threadIdx.x == 0) {
-        const float aN = cur[send];
-        if (!(aN > 0.f)) {
-            atomicMax(f.status, ST_ZERO);
+        if (f.phiN) {
+            // log P = log Z_N - theta tau log 2 + log sum_m phiN(m) alpha^_N(m) 2^{-theta m},
+            // the sum formed in FP64 relative to its largest term
+            const double th = (double)theta;
+            double lmax = -1e300;
+            for (int s = 0; s < M; ++s)
+                if (f.phiN[s] > 0.f && cur[s] > 0.f)
+                    lmax = fmax(lmax, log2((double)cur[s]) + log2((double)f.phiN[s]) -
+                                          th * (double)(s - xmax));
+            double sum = 0.0;
+            if (lmax > -1e300)
+                for (int s = 0; s < M; ++s)
+                    if (f.phiN[s] > 0.f && cur[s] > 0.f)
+                        sum += exp2(log2((double)cur[s]) + log2((double)f.phiN[s]) -
+                                    th * (double)(s - xmax) - lmax);
+            if (!(sum > 0.0)) {
+                atomicMax(f.status, ST_ZERO);
+            } else {
+                *f.loglik = (lmax + log2(sum) + (double)zexp + ztilt -
+                             th * (double)((long long)n * N)) * 0.6931471805599453;
+            }
         } else {
-            *f.loglik = log((double)aN) +
-                        ((double)zexp + ztilt - (double)theta * (double)rho) * 0.6931471805599453;
+            const float aN = cur[send];
+            if (!(aN > 0.f)) {
+                atomicMax(f.status, ST_ZERO);
+            } else {
+                *f.loglik = log((double)aN) +
+                            ((double)zexp + ztilt - (double)theta * (double)rho) * 0.6931471805599453;
+            }
         }
     }
 }

@@ -140,6 +140,8 @@ struct FrameHost {
     bool store = false;     // keep the receiver metrics in HBM for the APP producer
     bool tc = false;        // forward producer on the tensor cores
     bool tcb = false;       // APP producer on the tensor cores
+    std::vector<float> phi0, phiN;  // boundary drift priors (stream decoding), or empty
+    int64_t phi_off = 0;    // float offset of phi0 (then phiN) in the batch's buffer
 };
 
 // Stored receiver metrics of a frame: T tiles of P*MN rows x roundup4(q) floats.
@@ -303,13 +305,15 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
     f.chainStages = stages;
 }
 
-// Forward tile of the tensor-core producer: up to one lattice per thread
-// (Pf <= 256 / q positions), at most 256 symbols from the 8-aligned first one
-// (the MMA's N), the shared memory within the two-CTA budget.  Sets Pf, Sf,
-// Tf; false if no tile fits (the CUDA-core producer is used).
+// Forward tile of the tensor-core producer: up to two lattices per thread
+// (Pf <= 512 / q positions), at most 256 symbols from the 8-aligned first one
+// (the MMA's N), the shared memory within the two-CTA budget: frames with wide
+// drift limits get short tiles (their priors block is large), narrow ones long
+// tiles.  Sets Pf, Sf, Tf; false if no tile fits (the CUDA-core producer is
+// used).
 bool plan_fwd_tc(FrameDev &f) {
     if (!fwd_tc_supported(f.q, f.n, f.I)) return false;
-    for (int P = std::max(1, 256 / f.q); P >= 1; --P) {
+    for (int P = std::max(1, 512 / f.q); P >= 1; --P) {
         FrameDev t = f;
         t.Pf = P;
         t.Sf = (int)std::min<long long>(((long long)P - 1 + 2LL * f.xmax) / f.n + 2, f.N);
@@ -398,6 +402,8 @@ double frame_cost(const FrameDev &f) {
 using ClassKey = std::tuple<int, int, int>;  // n, I, tensor-core bits (kTcFwd | kTcBwd)
 
 constexpr int kTcFwd = 1, kTcBwd = 2;  // ClassKey / FrameHost tensor-core bits
+constexpr int kTcMinSymbols = 48;      // default rule: tensor-core forward producer from this
+                                       // many symbols per tile
 constexpr int kPerSym = 4;             // ClassKey: per-symbol-codebook producers
 
 struct ClassLaunch {
@@ -456,6 +462,8 @@ struct mapdec_batch {
     int *d_status = nullptr;
     uint32_t *d_rxw = nullptr;
     uint32_t *d_cw = nullptr;
+    float *d_phi = nullptr;       // boundary drift priors of the frames that have them
+    int64_t phi_total = 0;
     float *d_scratch = nullptr;
     size_t scratch_floats = 0;   // largest wave's scratch
     size_t region_floats = 0;    // stride between rotating scratch regions
@@ -508,10 +516,13 @@ struct mapdec {
     mapdec_batch *b = nullptr;      // decode (APPs, extrinsic outputs), made by mapdec_create
     mapdec_batch *bg = nullptr;     // gradient mode, made by the first mapdec_loglik_grad
     float *d_rout = nullptr;        // receiver-metric dump, (rho_max+1)*q*MN floats, first use
+    float *d_phi = nullptr;         // boundary drift priors: start, end (2 M floats), at create
+    bool use_phi0 = false, use_phiN = false;
     ~mapdec() {
         delete b;
         delete bg;
         if (d_rout) cudaFree(d_rout);
+        if (d_phi) cudaFree(d_phi);
     }
 };
 
@@ -618,6 +629,30 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         const long long tau = (long long)h.d.n * h.d.N;
         if (h.d.rx_len < 0) return MAPDEC_ERR_ARG;
         if (std::llabs(h.d.rx_len - tau) > h.d.xmax) return MAPDEC_ERR_DRIFT_RANGE;
+        {
+            // boundary drift priors (stream decoding): host or device, copied here
+            const int M = 2 * h.d.xmax + 1;
+            auto read_prior = [&](const float *src, std::vector<float> &dst) -> int {
+                if (!src) return MAPDEC_OK;
+                dst.resize(M);
+                if (is_device_ptr(src)) {
+                    CK(cudaMemcpy(dst.data(), src, (size_t)M * 4, cudaMemcpyDeviceToHost));
+                } else {
+                    std::memcpy(dst.data(), src, (size_t)M * 4);
+                }
+                double tot = 0.0;
+                for (float v : dst) {
+                    if (!(v >= 0.f) || !std::isfinite(v)) return MAPDEC_ERR_ARG;
+                    tot += v;
+                }
+                return tot > 0.0 ? MAPDEC_OK : MAPDEC_ERR_ARG;
+            };
+            st = read_prior(h.d.drift_start, h.phi0);
+            if (!st) st = read_prior(h.d.drift_end, h.phiN);
+            if (st) return st;
+            h.d.drift_start = nullptr;
+            h.d.drift_end = nullptr;
+        }
         const bool per_sym = h.d.codebook_per_symbol != 0;
         if (h.d.codebook_per_symbol != 0 && h.d.codebook_per_symbol != 1) return MAPDEC_ERR_ARG;
         if (per_sym && (h.d.q > kPsMaxQ || (flags & MAPDEC_BATCH_SEGMENTED)))
@@ -658,8 +693,10 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         // (about 2^-16 per product) leaves it 3e-4 off relative on small
         // gradients, where the FP32 W meets 1e-4.  MAPDEC_TC=0 keeps every frame
         // on the CUDA-core producers (A/B tests).
-        bool tc_on = tuned && tu.tensor_cores == 1;
-        if (const char *e = std::getenv("MAPDEC_TC")) tc_on = std::atoi(e) != 0;
+        // 0: the planner's rule, 1: wherever the class supports them, 2: never
+        int tc_mode = tuned ? tu.tensor_cores : 0;
+        if (const char *e = std::getenv("MAPDEC_TC")) tc_mode = std::atoi(e) != 0 ? 1 : 2;
+        bool tc_on = tc_mode != 2;
         if (tuned && (tu.chain_threads == 128 || tu.chain_threads == 256 ||
                       tu.chain_threads == 512))
             b->chain_threads = tu.chain_threads;
@@ -677,9 +714,25 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             tc_on = false;
         }
         h.tc = tc_on && !h.store && !b->grad && plan_fwd_tc(h.dev);
+        if (h.tc && tc_mode == 0) {
+            // the planner's rule: the tensor-core forward producer pays for its
+            // per-tile work (bf16 splits, priors block, MMA wait) once a tile
+            // spans many symbols, i.e. the CUDA-core contraction (S q per
+            // (position, length)) outweighs the lattices (measured crossover)
+            int smin = kTcMinSymbols;
+            if (const char *e = std::getenv("MAPDEC_TC_MIN_S")) smin = std::atoi(e);
+            if (h.dev.Sf < smin) {
+                h.tc = false;
+                h.dev.Pf = h.dev.P;
+                h.dev.Sf = h.dev.S;
+                h.dev.Tf = h.dev.T;
+            }
+        }
         if (h.tc) h.dev.Pgroups = prior_split_groups(h.dev);
-        bool tcb_on = tc_on;
-        if (const char *e = std::getenv("MAPDEC_TC_BWD")) tcb_on = tcb_on && std::atoi(e) != 0;
+        // the tensor-core APP producer only when asked for (it does not beat
+        // the CUDA-core one on the mixed workload)
+        bool tcb_on = tc_mode == 1;
+        if (const char *e = std::getenv("MAPDEC_TC_BWD")) tcb_on = tc_on && std::atoi(e) != 0;
         h.tcb = tcb_on && h.tc && !b->grad && plan_bwd_tc(h.dev);
         if (flags & MAPDEC_BATCH_SEGMENTED) {
             int K = (int)std::ceil(std::sqrt((double)h.d.N));
@@ -704,6 +757,8 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         b->rxw_total += (h.d.rx_len + 31) / 32 + 4;
         h.cw_off = b->cw_total;
         b->cw_total += (int64_t)h.cw.size();
+        h.phi_off = b->phi_total;
+        b->phi_total += (int64_t)(h.phi0.size() + h.phiN.size());
     }
     // resident buffers
     b->d_rx = (uint8_t *)b->dalloc(b->rx_total + 64);
@@ -722,6 +777,15 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
         std::vector<uint32_t> cwall(b->cw_total);
         for (auto &h : b->fr) std::copy(h.cw.begin(), h.cw.end(), cwall.begin() + h.cw_off);
         CK(cudaMemcpy(b->d_cw, cwall.data(), cwall.size() * 4, cudaMemcpyHostToDevice));
+    }
+    if (b->phi_total > 0) {
+        b->d_phi = (float *)b->dalloc((size_t)b->phi_total * 4);
+        std::vector<float> all((size_t)b->phi_total);
+        for (auto &h : b->fr) {
+            std::copy(h.phi0.begin(), h.phi0.end(), all.begin() + h.phi_off);
+            std::copy(h.phiN.begin(), h.phiN.end(), all.begin() + h.phi_off + h.phi0.size());
+        }
+        CK(cudaMemcpy(b->d_phi, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
     }
     // Scratch budget and waves (frames kept in order; a wave is a contiguous
     // range).  If everything fits, one wave; otherwise waves rotate over three
@@ -772,6 +836,8 @@ int build_batch(mapdec_batch *b, const mapdec_frame_desc_t *frames, int nf, int 
             FrameDev f = h.dev;
             f.rxbits = b->d_rxw + h.rxw_off;
             f.cw = b->d_cw + h.cw_off;
+            f.phi0 = h.phi0.empty() ? nullptr : b->d_phi + h.phi_off;
+            f.phiN = h.phiN.empty() ? nullptr : b->d_phi + h.phi_off + h.phi0.size();
             f.priors = b->d_priors + h.sym_off;
             float *base = b->d_scratch + off;
             size_t o = 0;
@@ -936,10 +1002,6 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
         mark(w, 0, 0, st);
         CK(launch_pack(wv.d_frames, wv.d_rxptr, wv.d_rxwptr, wv.f1 - wv.f0, wv.max_words, st));
         ++launches;
-        if (wv.prior_split_threads > 0) {
-            CK(launch_prior_split(wv.d_frames, wv.f1 - wv.f0, wv.prior_split_threads, st));
-            ++launches;
-        }
         mark(w, 0, 1, st);
     }
     CK(cudaEventRecord(fork, st));
@@ -947,6 +1009,12 @@ int64_t enqueue_run(mapdec_batch *b, bool grad, cudaStream_t st) {
     auto forward = [&](int w) {
         Wave &wv = b->waves[w];
         mark(w, 1, 0, st);
+        // the wave's priors split for the tensor-core producers, into the wave's
+        // own scratch region (so only once its previous user is done with it)
+        if (wv.prior_split_threads > 0) {
+            CK(launch_prior_split(wv.d_frames, wv.f1 - wv.f0, wv.prior_split_threads, st));
+            ++launches;
+        }
         for (auto &c : wv.cls) {
             CK(c.ps   ? launch_fwd_ps(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, st)
                : c.tc ? launch_fwd_tc(c.n, c.I, wv.d_frames, c.d_fwd, c.nfwd, c.smem_fwd, st)
@@ -1510,10 +1578,17 @@ int mapdec_create(mapdec_t **out, int q, int n, const uint8_t *codebook, int N, 
     d.codebook = h->codebook.data();
     d.rx_len = h->rho_max;
     d.codebook_per_symbol = 0;
+    d.drift_start = nullptr;
+    d.drift_end = nullptr;
     st = mapdec_batch_create(&h->b, &d, 1, MAPDEC_BATCH_PLAIN | MAPDEC_BATCH_EXTRINSIC, 0);
     if (st) {
         delete h;
         return st;
+    }
+    if (cudaMalloc(&h->d_phi, (size_t)2 * (2 * xmax + 1) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return MAPDEC_ERR_NOMEM;
     }
     *out = h;
     return MAPDEC_OK;
@@ -1533,9 +1608,12 @@ namespace {
 // rho_max >= rho): the descriptor gets rho and its tile counts, the producer
 // launches their prefix of the work lists, and the extrinsic output pointer is
 // set only when asked for.  Nothing is allocated.
-void retarget_single(mapdec_batch *b, int64_t rho, bool ext) {
+void retarget_single(mapdec_batch *b, int64_t rho, bool ext, const float *phi0,
+                     const float *phiN) {
     FrameHost &h = b->fr[0];
     FrameDev &f = h.dev;
+    f.phi0 = phi0;
+    f.phiN = phiN;
     h.d.rx_len = rho;
     f.rho = rho;
     if (!f.ps) {  // per-symbol work items do not depend on rho
@@ -1566,12 +1644,16 @@ static int ensure_single(mapdec_t *h, int64_t rho, bool grad, bool ext = false) 
         d.codebook = h->codebook.data();
         d.rx_len = h->rho_max;
         d.codebook_per_symbol = 0;
+        d.drift_start = nullptr;
+        d.drift_end = nullptr;
         int st = mapdec_batch_create(&h->bg, &d, 1, MAPDEC_BATCH_PLAIN | MAPDEC_BATCH_GRAD, 0);
         if (st) return st;
         h->bg->stream = h->stream;
     }
     try {
-        retarget_single(grad ? h->bg : h->b, rho, ext);
+        const int M = 2 * h->xmax + 1;
+        retarget_single(grad ? h->bg : h->b, rho, ext, h->use_phi0 ? h->d_phi : nullptr,
+                        h->use_phiN ? h->d_phi + M : nullptr);
     } catch (CudaErr &e) {
         cudaGetLastError();
         return map_cuda(e.e);
@@ -1633,6 +1715,38 @@ int mapdec_receiver_metric(mapdec_t *h, const uint8_t *rx, int64_t rx_len, float
     }
 }
 
+int mapdec_set_drift_priors(mapdec_t *h, const float *drift_start, const float *drift_end) {
+    if (!h) return MAPDEC_ERR_ARG;
+    const int M = 2 * h->xmax + 1;
+    std::vector<float> v((size_t)M);
+    const float *src[2] = {drift_start, drift_end};
+    for (int k = 0; k < 2; ++k) {
+        if (!src[k]) continue;
+        if (is_device_ptr(src[k])) {
+            if (cudaMemcpy(v.data(), src[k], (size_t)M * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cudaGetLastError();
+                return MAPDEC_ERR_CUDA;
+            }
+        } else {
+            std::memcpy(v.data(), src[k], (size_t)M * 4);
+        }
+        double tot = 0.0;
+        for (float x : v) {
+            if (!(x >= 0.f) || !std::isfinite(x)) return MAPDEC_ERR_ARG;
+            tot += x;
+        }
+        if (!(tot > 0.0)) return MAPDEC_ERR_ARG;
+        if (cudaMemcpy(h->d_phi + (size_t)k * M, v.data(), (size_t)M * 4,
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return MAPDEC_ERR_CUDA;
+        }
+    }
+    h->use_phi0 = drift_start != nullptr;
+    h->use_phiN = drift_end != nullptr;
+    return MAPDEC_OK;
+}
+
 void mapdec_destroy(mapdec_t *h) { delete h; }
 
 int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_dev,
@@ -1642,7 +1756,7 @@ int mapdec_decode_noalloc(const mapdec_frame_desc_t *frame, const uint8_t *rx_de
     const mapdec_frame_desc_t &d = *frame;
     int st = validate(d.q, d.n, d.N, d.Pi, d.Pd, d.Ps, d.I, d.xmax);
     if (st) return st;
-    if (d.codebook_per_symbol) return MAPDEC_ERR_UNSUPPORTED;
+    if (d.codebook_per_symbol || d.drift_start || d.drift_end) return MAPDEC_ERR_UNSUPPORTED;
     if (d.q > kStaticMaxQ) return MAPDEC_ERR_TOO_LARGE;
     const long long tau = (long long)d.n * d.N;
     if (d.rx_len < 0) return MAPDEC_ERR_ARG;

@@ -61,6 +61,10 @@ struct FrameDev {
     int Pgroups;  // tensor-core forward producer: 8-row groups of Pbuf
     unsigned char *Pbuf;  // the priors split into three bf16 pieces in that
                           // producer's operand layout (k_prior_split), or null
+    // Stream decoding: drift priors of the frame's start and end (M floats each,
+    // index m + xmax) replacing alpha_0 = [m = 0] and beta_N = [m = rho - tau];
+    // null for an isolated frame.
+    const float *phi0, *phiN;
     int nsub;     // sub-tiles per backward super-tile
     int S2;       // max symbols touched by one super-tile (rows of Lp per super-tile)
     int T2;       // backward super-tiles: ceil(T / nsub)

@@ -187,23 +187,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restri
     const int lg = warp & 3, half = warp >> 2;
     for (int t = 0; t < MT && issued; ++t) {
         const int buf = t % nbuf;
-        if (!tc_wait(&s_bar[buf], (uint32_t)((t / nbuf) & 1))) s_fail = ST_TIMEOUT;
+        // one thread waits for the MMAs (bounded); the others wait at the CTA
+        // barrier, which takes no issue slots from the co-resident CTA
+        if (tid == 0 && !tc_wait(&s_bar[buf], (uint32_t)((t / nbuf) & 1))) s_fail = ST_TIMEOUT;
+        tc::fence_before_sync();
+        __syncthreads();
         tc::fence_after_sync();
         const int m = t * 128 + lg * 32 + lane;
         const int pl = m / MNp, j = m - pl * MNp;
         const long long p = p0 + pl;
-        const bool rowok = pl < P && j < MN && p <= rho && !s_fail;
-        const long long sbase = p - (long long)n * ilo8 + xmax;  // drift state for c = 0
+        // this row's symbols: drift state s = p + xmax - n i inside [0, M), so
+        // i in [ceil((p + xmax - M + 1) / n), floor((p + xmax) / n)], within the tile's
+        const long long pw = p + xmax;
+        int clo = (int)max((long long)ilo, ceildiv(pw - M + 1, n)) - ilo8;
+        int chi = (int)min((long long)ihi, floordiv(pw, n)) - ilo8;
+        if (!(pl < P && j < MN && p <= rho) || s_fail) chi = -1;  // nothing to store
+        // W[i][s][j] = W + pw MNS + j + i (wblk - n MNS)
+        float *wrow = f.W + (size_t)pw * f.MNS + j + (size_t)ilo8 * (f.wblk - (long long)n * f.MNS);
+        const long long wstep = f.wblk - (long long)n * f.MNS;
         const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * 128);
         for (int c0 = half * 16; c0 < NNa; c0 += 32) {
             float v[16];
             tc::ld16(ta + (uint32_t)c0, v);
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                const int i = ilo8 + c0 + e;
-                const long long s = sbase - (long long)n * (c0 + e);
-                if (rowok && i >= ilo && i <= ihi && s >= 0 && s < M)
-                    f.W[(size_t)i * f.wblk + s * f.MNS + j] = v[e];
+                const int c = c0 + e;
+                if (c >= clo && c <= chi) wrow[(long long)c * wstep] = v[e];
             }
         }
         tc::fence_before_sync();
@@ -302,7 +311,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restri
     bool issued = false;   // the accumulator holds data
     auto drain = [&]() {
         if (pending) {
-            if (!tc_wait(&s_bar, phase)) s_fail = ST_TIMEOUT;
+            // one thread waits (bounded); the others at the CTA barrier
+            if (tid == 0 && !tc_wait(&s_bar, phase)) s_fail = ST_TIMEOUT;
+            tc::fence_before_sync();
+            __syncthreads();
             phase ^= 1u;
             pending = false;
             tc::fence_after_sync();

@@ -50,7 +50,8 @@ class FrameDesc(ctypes.Structure):
                 ("I", ctypes.c_int), ("xmax", ctypes.c_int), ("Pi", ctypes.c_double),
                 ("Pd", ctypes.c_double), ("Ps", ctypes.c_double),
                 ("codebook", ctypes.c_void_p), ("rx_len", ctypes.c_int64),
-                ("codebook_per_symbol", ctypes.c_int)]
+                ("codebook_per_symbol", ctypes.c_int), ("drift_start", ctypes.c_void_p),
+                ("drift_end", ctypes.c_void_p)]
 
 
 _lib = None
@@ -85,6 +86,7 @@ _SIGS = {
     "mapdec_batch_phase_ms": (ctypes.c_int, [_VP, _VP]),
     "mapdec_batch_num_waves": (ctypes.c_int, [_VP]),
     "mapdec_batch_tc_frames": (ctypes.c_int, [_VP, _VP]),
+    "mapdec_set_drift_priors": (ctypes.c_int, [_VP, _VP, _VP]),
     "mapdec_fp32_fma_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _VP]),
     "mapdec_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
     "mapdec_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
@@ -191,6 +193,11 @@ def mapdec_receiver_metric(h, rx, rx_len, R_out):
     return load().mapdec_receiver_metric(h, _ptr(rx), int(rx_len), _ptr(R_out))
 
 
+def mapdec_set_drift_priors(h, drift_start, drift_end):
+    _check(load().mapdec_set_drift_priors(h, _ptr(drift_start), _ptr(drift_end)),
+           "mapdec_set_drift_priors")
+
+
 def mapdec_destroy(h):
     load().mapdec_destroy(h)
 
@@ -214,10 +221,20 @@ def mapdec_batch_create(frames, flags=0, mem_budget_bytes=0):
         cb = np.ascontiguousarray(fr.codebook, dtype=np.uint8)
         keep.append(cb)
         rho = fr.rho if hasattr(fr, "rho") else int(fr.rx_len)
-        # a (q, n) codebook serves every symbol; (N, q, n) gives one per symbol
+        # a (q, n) codebook serves every symbol; (N, q, n) gives one per symbol;
+        # optional boundary drift priors (stream decoding): fr.drift_start / drift_end
+        bounds = []
+        for name in ("drift_start", "drift_end"):
+            v = getattr(fr, name, None)
+            if v is None:
+                bounds.append(None)
+            else:
+                a = np.ascontiguousarray(v, dtype=np.float32)
+                keep.append(a)
+                bounds.append(a.ctypes.data)
         arr[k] = FrameDesc(int(fr.q), int(fr.n), int(fr.N), int(fr.I), int(fr.xmax),
                            float(fr.Pi), float(fr.Pd), float(fr.Ps), cb.ctypes.data, int(rho),
-                           1 if cb.ndim == 3 else 0)
+                           1 if cb.ndim == 3 else 0, bounds[0], bounds[1])
     b = _VP()
     _check(lib.mapdec_batch_create(ctypes.byref(b), arr, len(frames), int(flags),
                                    int(mem_budget_bytes)), "mapdec_batch_create")
@@ -392,6 +409,14 @@ class Decoder:
 
     def set_stream(self, stream):
         mapdec_set_stream(self.h, stream)
+
+    def set_drift_priors(self, drift_start=None, drift_end=None):
+        """Stream decoding: priors (2 xmax + 1 each, index m + xmax) of the drift
+        at the frame's start and end for the following calls; None = the
+        isolated frame's boundary."""
+        a = None if drift_start is None else np.ascontiguousarray(drift_start, np.float32)
+        b = None if drift_end is None else np.ascontiguousarray(drift_end, np.float32)
+        mapdec_set_drift_priors(self.h, a, b)
 
     def receiver_metric(self, rx, MN):
         rx = np.ascontiguousarray(rx, dtype=np.uint8)

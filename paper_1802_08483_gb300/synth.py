@@ -55,6 +55,10 @@ class Frame:
     priors: Optional[np.ndarray]  # (N, q) float32, or None for uniform
     rx: np.ndarray                # (rho,) uint8 0/1
     tag: str = ""
+    # stream decoding: priors of the drift at the frame's start and end
+    # (2 xmax + 1 each, index m + xmax), or None for an isolated frame
+    drift_start: Optional[np.ndarray] = None
+    drift_end: Optional[np.ndarray] = None
 
     @property
     def rho(self) -> int:
@@ -152,6 +156,34 @@ def per_symbol_frame(rng: np.random.Generator, q: int, n: int, N: int, I: int, x
         raise RuntimeError("could not draw a realisation within the drift limit")
     return Frame(q=q, n=n, N=N, I=I, xmax=xmax, Pi=float(Pi), Pd=float(Pd), Ps=float(Ps),
                  codebook=books, message=msg.astype(np.int64), priors=priors, rx=rx, tag=tag)
+
+
+def _gauss_window(xmax: int, centre: float, sd: float, lo: int, hi: int) -> np.ndarray:
+    """Discretised Gaussian over drift states m in [lo, hi] (index m + xmax)."""
+    m = np.arange(-xmax, xmax + 1)
+    w = np.exp(-0.5 * ((m - centre) / sd) ** 2)
+    w[(m < lo) | (m > hi)] = 0.0
+    return (w / w.sum()).astype(np.float32)
+
+
+def stream_frame(rng: np.random.Generator, q: int, n: int, N: int, I: int, xmax: int,
+                 Pi: float, Pd: float, Ps: float, pre: int, post: int, sd: float,
+                 tag: str = "") -> Frame:
+    """A frame cut from a stream: `pre` bits of the previous frame before it and
+    `post` bits of the next one after it.  The boundary drift priors are
+    discretised Gaussians of width sd around the true start (drift pre) and the
+    true end, over the states the received bits allow."""
+    fr = make_frame(rng, q, n, N, I, max(1, xmax - pre - post), Pi, Pd, Ps, dirichlet=True,
+                    tag=tag)
+    body = fr.rx
+    rx = np.concatenate([rng.integers(0, 2, pre), body, rng.integers(0, 2, post)]).astype(np.uint8)
+    tau = n * N
+    end = pre + body.size - tau  # true end drift
+    fr.rx = rx
+    fr.xmax = xmax
+    fr.drift_start = _gauss_window(xmax, pre, sd, 0, xmax)
+    fr.drift_end = _gauss_window(xmax, end, sd, -xmax, rx.size - tau)
+    return fr
 
 
 def c3_params(rng: np.random.Generator):

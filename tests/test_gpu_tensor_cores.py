@@ -100,3 +100,24 @@ def test_single_frame_handle_uses_tensor_cores(monkeypatch):
     check_app(app, app_ref)
     check_ll(ll, ll_ref)
     dec.close()
+
+
+def test_tensor_cores_across_waves(monkeypatch):
+    """A scratch budget of one frame per wave: the waves rotate over three
+    scratch regions, and every wave's priors are split for the tensor cores in
+    its own region before its forward producers run."""
+    monkeypatch.setenv("MAPDEC_TC", "1")
+    frames = _frames()
+    b = mapdec.Batch(frames, flags=mapdec.MAPDEC_BATCH_GRAPH, mem_budget_bytes=1 << 20)
+    assert mapdec.mapdec_batch_num_waves(b.b) >= 4
+    rx, pr = b.concat_inputs()
+    for rep in range(2):
+        st, app, ll = b.decode(rx, pr)
+        assert st == 0, mapdec.mapdec_strerror(st)
+        apps = b.split(app)
+        for k, fr in enumerate(frames):
+            app_ref, ll_ref = oracle.decode(fr.codebook, fr.N, fr.Pi, fr.Pd, fr.Ps, fr.I,
+                                            fr.xmax, fr.rx, priors=fr.priors, kappa=2.0)
+            check_app(apps[k], app_ref, what=f"case {TC_CASES[k][0]} rep {rep}")
+            check_ll(ll[k], ll_ref, what=f"case {TC_CASES[k][0]} rep {rep}")
+    b.close()
