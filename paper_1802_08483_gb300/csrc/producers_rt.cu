@@ -138,7 +138,8 @@ size_t fwd_tc_smem_bytes(const FrameDev &f) {
 }
 
 size_t bwd_tc_smem_bytes(const FrameDev &f) {
-    const size_t K = (size_t)f.P * f.MN, Kp = (K + 15) & ~(size_t)15;
+    const size_t MNp = ((size_t)f.MN + 7) & ~(size_t)7;
+    const size_t K = (size_t)f.P * MNp, Kp = (K + 15) & ~(size_t)15;
     const size_t Smax4 = ((size_t)f.S + 3) & ~(size_t)3;
     const size_t BW = (size_t)f.P + f.MN - 1;
     const size_t b = 4 * (size_t)f.q * Kp + 4 * 128 * (size_t)kTcChunkCols +

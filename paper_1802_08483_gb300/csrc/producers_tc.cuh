@@ -236,18 +236,36 @@ namespace mdk {
 // Tensor-core APP producer (decode mode).  Same work item and output as k_bwd
 // (a super-tile of nsub sub-tiles of P positions; Lp rows of the super-tile's
 // symbols), with the contraction of eqs. (L), (sigma) on the tensor cores:
-//     C[il2][D] += sum_k A[il2][k] R[D][k],   k = pl * MN + j,
+//     C[il2][D] += sum_k A[il2][k] R[D][k],   k = pl * MNp + j,
 //     A[il2][k] = Aw[pl][il] Bw[pl + j][il]   (il = il2 - off: the sub-tile's
 //                                              symbols; other rows zero)
-// accumulated over every sub-tile in one TMEM accumulator of 128 lanes
-// (il2 < S2 <= 128) and q columns.  Both operands are split into bf16 hi + lo
-// and multiplied as hi*hi + hi*lo + lo*hi (FP32 accumulation).
-// Shared memory: Rhi, Rlo [q rows][Kp] (Kp = P*MN rounded up to 16, the pad
-// columns zero), Ahi, Alo [128 rows][kTcChunk] (A is built chunk by chunk of
-// kTcChunk columns and consumed by the MMAs before the next chunk), the
-// windows Aw, Bw (FP32) and the per-symbol tilt constants.
+// with MNp = MN rounded up to 8 (lengths j >= MN are zero columns of both
+// operands), accumulated over every sub-tile in one TMEM accumulator of 128
+// lanes (il2 < S2 <= 128) and q columns.  Two bf16 pieces, three products.
+// Shared memory: R, 2 pieces, K-major [q rows][Kp] (Kp = P MNp rounded up to
+// 16, the pad columns zero): a lattice thread stores 8 consecutive lengths as
+// one 16-byte row of a core matrix per piece; A, 2 pieces, [128 rows][kTcChunk],
+// built chunk by chunk, 8 columns (one position) per thread and row, and read
+// by the MMAs before the next chunk is built; the windows Aw, Bw (FP32) and the
+// per-symbol tilt constants.
 // ---------------------------------------------------------------------------
 constexpr int kTcChunk = kTcChunkCols;  // A-operand columns per chunk (a multiple of 16)
+
+// 8 values split into two bf16 pieces, each packed as 8 bf16 (16 bytes).
+__device__ __forceinline__ void split2_x8(const float (&v)[8], uint4 &p0, uint4 &p1) {
+    uint32_t w0[4], w1[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float a = v[2 * e], b = v[2 * e + 1];
+        const uint32_t h = pack_bf16x2(a, b);
+        a -= __uint_as_float(h << 16);
+        b -= __uint_as_float(h & 0xffff0000u);
+        w0[e] = h;
+        w1[e] = pack_bf16x2(a, b);
+    }
+    p0 = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    p1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+}
 
 template <int NB, int IB>
 __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restrict__ frames,
@@ -255,6 +273,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restri
     static_assert(NB > 0, "compile-time lattice only");
     constexpr int n = NB;
     constexpr int MN = NB * (IB + 1) + 1;
+    constexpr int MNp = (MN + 7) & ~7;
     const Work wk = work[blockIdx.x];
     const FrameDev &f = frames[wk.frame];
     const int q = f.q, P = f.P;
@@ -263,20 +282,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restri
     super_symbols(f, wk.tile, ilo2, ihi2);
     const int S2 = ihi2 - ilo2 + 1;
     if (S2 <= 0) return;  // uniform over the CTA, before any tensor memory is held
-    const int K = P * MN;
-    const int Kp = (K + 15) & ~15;
+    const int Kp = (P * MNp + 15) & ~15;
     const int kcR = Kp >> 3;
     constexpr int kcA = kTcChunk >> 3;
     const int BW = P + MN - 1;
     const int Smax4 = (f.S + 3) & ~3;
     const uint32_t ncols = q <= 32 ? 32u : 64u;
+    const size_t rpiece = (size_t)q * Kp * 2, apiece = (size_t)128 * kTcChunk * 2;
 
     extern __shared__ __align__(128) unsigned char tsm[];
-    unsigned char *Rhi = tsm;
-    unsigned char *Rlo = Rhi + (size_t)q * Kp * 2;
-    unsigned char *Ahi = Rlo + (size_t)q * Kp * 2;
-    unsigned char *Alo = Ahi + (size_t)128 * kTcChunk * 2;
-    float *Aw = reinterpret_cast<float *>(Alo + (size_t)128 * kTcChunk * 2);
+    unsigned char *R0 = tsm;  // pieces at R0, R0 + rpiece
+    unsigned char *A0 = R0 + 2 * rpiece;  // pieces at A0, A0 + apiece
+    float *Aw = reinterpret_cast<float *>(A0 + 2 * apiece);
     float *Bw = Aw + (size_t)P * Smax4;
     int *symE = reinterpret_cast<int *>(Bw + (size_t)BW * Smax4);
     float *symF = reinterpret_cast<float *>(symE + Smax4);
@@ -293,12 +310,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restri
         mbar_init(&s_bar, 1);
         fence_mbar_init();
     }
-    // pad columns K .. Kp-1 of R stay zero (the lattices write columns < K)
-    for (int e = tid; e < q * (Kp - K); e += kThreads) {
-        const int D = e / (Kp - K), k = K + e % (Kp - K);
-        const uint32_t o = tc::op_offset(D, k, kcR);
-        *reinterpret_cast<__nv_bfloat16 *>(Rhi + o) = __float2bfloat16_rn(0.f);
-        *reinterpret_cast<__nv_bfloat16 *>(Rlo + o) = __float2bfloat16_rn(0.f);
+    // the pad columns P MNp .. Kp-1 of R stay zero (the lattices write below them)
+    for (int e = tid; e < q * ((Kp - P * MNp) >> 3); e += kThreads) {
+        const int per = (Kp - P * MNp) >> 3;
+        const int D = e / per, g = P * MNp / 8 + e % per;
+        const uint32_t o = tc::op_offset(D, g * 8, kcR);
+        *reinterpret_cast<uint4 *>(R0 + o) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(R0 + rpiece + o) = make_uint4(0u, 0u, 0u, 0u);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -335,15 +353,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restri
         window_fetch(f, p0, n, ilo, S, S4, P, BW, Aw, Bw);
         drain();  // the previous sub-tile's MMAs have read R and A
 
-        // (A) lattices into R: a warp covers 4 positions x 8 codewords
-        // (conflict-free stores: MN is odd)
+        // (A) lattices into R: a warp covers 4 positions x 8 codewords; a quarter
+        // warp (one position) stores 8 consecutive 16-byte rows of a core matrix
         const int nblk = ((P + 3) >> 2) * (q >> 3);
         for (int b = warp; b < nblk; b += kThreads / 32) {
             const int pb = b / (q >> 3), db = b - pb * (q >> 3);
             const int pl = pb * 4 + (lane >> 3), D = db * 8 + (lane & 7);
             if (pl >= P) continue;
             const long long p = p0 + pl;
-            float v[kMaxMN];
+            float v[MNp];
             if (p <= rho) {
                 eval_metric<NB, IB, 0>(f, p, D, v);
             } else {
@@ -351,12 +369,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restri
                 for (int j = 0; j < MN; ++j) v[j] = 0.f;
             }
 #pragma unroll
-            for (int j = 0; j < MN; ++j) {
-                __nv_bfloat16 h, l;
-                tc::split_bf16(v[j], h, l);
-                const uint32_t o = tc::op_offset(D, pl * MN + j, kcR);
-                *reinterpret_cast<__nv_bfloat16 *>(Rhi + o) = h;
-                *reinterpret_cast<__nv_bfloat16 *>(Rlo + o) = l;
+            for (int j = MN; j < MNp; ++j) v[j] = 0.f;
+#pragma unroll
+            for (int c = 0; c < MNp / 8; ++c) {
+                float x[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = v[c * 8 + e];
+                uint4 a0, a1;
+                split2_x8(x, a0, a1);
+                const uint32_t o = tc::op_offset(D, pl * MNp + c * 8, kcR);
+                *reinterpret_cast<uint4 *>(R0 + o) = a0;
+                *reinterpret_cast<uint4 *>(R0 + rpiece + o) = a1;
             }
         }
         cp_async_wait_all();
@@ -364,46 +387,41 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restri
         window_tilt(S, S4, P, BW, Aw, Bw, symE, symF, symG, symPhi);
         __syncthreads();
 
-        // (C) A chunk by chunk: a thread builds 8 consecutive columns of one row
-        // (one 16-byte store per part); a warp covers 32 consecutive rows
+        // (C) A chunk by chunk: a thread builds the 8 columns of one position
+        // (one 16-byte store per piece); a warp covers 32 consecutive rows
+        const int kdata = P * MNp;  // columns holding positions; the rest stay zero
         for (int c0 = 0; c0 < Kp; c0 += kTcChunk) {
             const int w = min(kTcChunk, Kp - c0);
             drain();  // the previous chunk's MMAs have read A
             for (int u = tid; u < 128 * (w >> 3); u += kThreads) {
                 const int il2 = u & 127, g = u >> 7;
                 const int il = il2 - off;
-                uint32_t hw[4], lw[4];
+                const int k0 = c0 + g * 8;
+                uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = a0;
+                if (il >= 0 && il < S && k0 < kdata) {
+                    const int pl = k0 / MNp, j0 = k0 - pl * MNp;
+                    const float aw = Aw[pl * S4 + il];
+                    if (aw != 0.f) {
+                        float x[8];
 #pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    float a[2];
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        const int k = c0 + g * 8 + e + t;
-                        a[t] = 0.f;
-                        if (il >= 0 && il < S && k < K) {
-                            const int pl = k / MN, j = k - pl * MN;
-                            a[t] = Aw[pl * S4 + il] * Bw[(pl + j) * S4 + il];
+                        for (int e = 0; e < 8; ++e) {
+                            const int j = j0 + e;
+                            x[e] = j < MN ? aw * Bw[(pl + j) * S4 + il] : 0.f;
                         }
+                        split2_x8(x, a0, a1);
                     }
-                    __nv_bfloat16 h0, l0, h1, l1;
-                    tc::split_bf16(a[0], h0, l0);
-                    tc::split_bf16(a[1], h1, l1);
-                    hw[e >> 1] = (uint32_t)__bfloat16_as_ushort(h0) |
-                                 ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                    lw[e >> 1] = (uint32_t)__bfloat16_as_ushort(l0) |
-                                 ((uint32_t)__bfloat16_as_ushort(l1) << 16);
                 }
                 const uint32_t o = tc::op_offset(il2, g * 8, kcA);
-                *reinterpret_cast<uint4 *>(Ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4 *>(Alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                *reinterpret_cast<uint4 *>(A0 + o) = a0;
+                *reinterpret_cast<uint4 *>(A0 + apiece + o) = a1;
             }
             tc::fence_proxy_async();
             tc::fence_before_sync();
             __syncthreads();
             if (tid == 0) {
                 tc::fence_after_sync();
-                const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
-                const uint32_t rh = smem_u32(Rhi), rl = smem_u32(Rlo);
+                const uint32_t ah = smem_u32(A0), al = ah + (uint32_t)apiece;
+                const uint32_t rh = smem_u32(R0), rl = rh + (uint32_t)rpiece;
                 for (int k0 = 0; k0 < w; k0 += 16) {
                     const uint32_t ao = (uint32_t)(k0 >> 3) * 128u;
                     const uint32_t ro = (uint32_t)((c0 + k0) >> 3) * 128u;
