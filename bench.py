@@ -56,6 +56,18 @@ def lattice_cells(n, I):
     return (I + 1) * n * (n + 1) // 2 + n
 
 
+def lattices(fr) -> int:
+    """Receiver-metric lattices a frame needs: one per (rx start p, codeword D)
+    with one codebook; with one codebook per symbol the metric also depends on
+    i, so one per (i, s', D) with start position n i + s' - xmax in [0, rho]."""
+    if np.ndim(fr.codebook) == 3:
+        i = np.arange(fr.N, dtype=np.int64)
+        lo = np.maximum(0, fr.xmax - fr.n * i)
+        hi = np.minimum(2 * fr.xmax, fr.rho - fr.n * i + fr.xmax)
+        return int(np.maximum(hi - lo + 1, 0).sum()) * fr.q
+    return (fr.rho + 1) * fr.q
+
+
 def valid_transitions(fr) -> int:
     """Number of (i, s', j) with start position in [0, rho], end drift inside the
     limits and window inside the received sequence."""
@@ -118,7 +130,7 @@ def frame_flops(fr) -> dict:
     backward phase.  The backward phase also re-evaluates every lattice (it
     recomputes R instead of storing it): executed work, reported apart as
     "backward_recompute", never as algorithmic."""
-    lat = (fr.rho + 1) * fr.q * lattice_cells(fr.n, fr.I) * (2 * fr.I + 3)
+    lat = lattices(fr) * lattice_cells(fr.n, fr.I) * (2 * fr.I + 3)
     V = valid_transitions(fr)
     return {"forward": lat + 2 * fr.q * V, "chains": 4 * V, "backward": 2 * fr.q * V,
             "backward_recompute": lat, "lattice": lat, "V": V}
@@ -309,7 +321,7 @@ def _time_ms(fn, reps=5, warm=2):
     return best
 
 
-def run_configs(fp32_peak, which=(1, 2, 4, 5)):
+def run_configs(fp32_peak, which=(1, 2, 4, 5, 6, 7)):
     import torch
     from paper_1802_08483_gb300 import mapdec
     out = []
@@ -378,6 +390,25 @@ def run_configs(fp32_peak, which=(1, 2, 4, 5)):
         b.close()
     if key is not None:
         mapdec.mapdec_tune_set(*key, None)
+    if 6 in which:
+        # one codebook per symbol: lattices on the (i, s', D) grid, no position dedupe
+        frames = synth.config_frames(6)
+        b, fn = batch_run(frames, mapdec.MAPDEC_BATCH_GRAPH)
+        ms = _time_ms(fn, reps=3, warm=1)
+        report("config 6: 64 frames N=1000, q=16, n=10, one codebook per symbol, decode",
+               frames, ms, flops_of(frames),
+               {"executed_tflops": (flops_of(frames) + sum(frame_flops(f)["lattice"]
+                                                          for f in frames)) / (ms / 1e3) / 1e12,
+                "lattices_per_frame": lattices(frames[0])})
+        b.close()
+    if 7 in which:
+        # frames cut from a stream, drift priors on both boundaries, extrinsic outputs
+        frames = synth.config_frames(7)
+        b, fn = batch_run(frames, mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_EXTRINSIC)
+        ms = _time_ms(fn, reps=3, warm=1)
+        report("config 7: 256 frames N=1000, q=16, n=10 cut from a stream, boundary drift "
+               "priors, APPs + extrinsic outputs", frames, ms, flops_of(frames))
+        b.close()
     if 4 not in which and 5 not in which:
         return out
     # config 4: 256 frames, log-likelihood and gradients, alpha checkpoint every 45 symbols
@@ -428,9 +459,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=20.0)
-    ap.add_argument("--configs", nargs="?", const="1,2,4,5", default=None,
+    ap.add_argument("--configs", nargs="?", const="1,2,4,5,6,7", default=None,
                     help="instead of the benchmark line, report synthetic configurations "
-                         "(comma list; default 1,2,4,5)")
+                         "(comma list; default 1,2,4,5,6,7)")
     ap.add_argument("--tuning", default=DEFAULT_TUNING,
                     help="tuning table (JSON written by paper_1802_08483_gb300.tune); '' = none")
     ap.add_argument("--log-jsonl", default="",
@@ -583,7 +614,7 @@ def main():
     value = total_bits / (ms / 1e3)
     phase_ms = phase_tot / steps
 
-    # ---- roofline of the dominant phase (FP32 CUDA-core arithmetic) ----
+    # ---- roofline of the dominant phase, per pipe (FP32 CUDA cores, tensor cores) ----
     props = torch.cuda.get_device_properties(local_rank)
     peaks = {}
     try:
@@ -631,8 +662,9 @@ def main():
                           "tensor": {"achieved": tens_t, "peak": tensor_peak, "frac": tens_frac,
                                      "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained "
                                                     "(cuBLAS bf16, of measured)",
-                                     "executed_products": 3,
-                                     "note": "split bf16: three MMAs per algorithmic product"}},
+                                     "executed_products": {"forward": 6, "backward": 3},
+                                     "note": "split bf16: six (W) or three (APP) bf16 MMAs "
+                                             "per algorithmic product, counted once"}},
                 "executed_fp32": {"tflops": (pf.get("executed_fp32", pf["fp32"]) / sec / 1e12)
                                   if sec > 0 else 0.0,
                                   "note": "adds the lattices the APP producer recomputes "

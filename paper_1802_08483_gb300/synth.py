@@ -196,7 +196,7 @@ def c3_params(rng: np.random.Generator):
 
 
 def config_frame(config: int, frame: int) -> Frame:
-    """Frame `frame` of workload `config` (1..5), fully determined by its seed."""
+    """Frame `frame` of workload `config` (1..7), fully determined by its seed."""
     rng = np.random.default_rng(frame_seed(config, frame))
     if config == 1:
         return make_frame(rng, 16, 10, 50, 2, 20, 0.01, 0.01, 0.0, tag="c1")
@@ -214,10 +214,20 @@ def config_frame(config: int, frame: int) -> Frame:
         cb = random_codebook(cb_rng, 64, 12)
         return make_frame(rng, 64, 12, 8000, 3, 830, 0.1, 0.1, 0.01, codebook=cb,
                           dirichlet=True, tag=f"c5/{frame}")
+    if config == 6:
+        # one codebook per symbol (Sec. II-A), N=1000, q=16, n=10, xmax by the
+        # mixed workload's rule: ceil(6 sqrt(N n (Pi + Pd))) = 85
+        return per_symbol_frame(rng, 16, 10, 1000, 2, 85, 0.01, 0.01, 0.001, tag=f"c6/{frame}")
+    if config == 7:
+        # frames cut from a stream: up to 8 bits of each neighbour inside the
+        # received window, Gaussian drift priors (sd 3 bits) on both boundaries
+        pre, post = int(rng.integers(0, 9)), int(rng.integers(0, 9))
+        return stream_frame(rng, 16, 10, 1000, 2, 85, 0.01, 0.01, 0.001, pre, post, 3.0,
+                            tag=f"c7/{frame}")
     raise ValueError(f"unknown workload {config}")
 
 
-CONFIG_FRAMES = {1: 1, 2: 1, 3: 4096, 4: 256, 5: 64}
+CONFIG_FRAMES = {1: 1, 2: 1, 3: 4096, 4: 256, 5: 64, 6: 64, 7: 256}
 
 
 def config_frames(config: int, frames: Optional[List[int]] = None) -> List[Frame]:

@@ -85,3 +85,18 @@ def test_pipe_flops_split():
         assert pf["forward"]["tensor"] == (w if bits & 1 else 0)
         assert pf["backward"]["tensor"] == (w if bits & 2 else 0)
         assert pf["backward"]["executed_fp32"] == pf["backward"]["fp32"] + ff["lattice"]
+
+
+@pytest.mark.parametrize("seed,N,xmax", [(61, 7, 5), (62, 30, 12), (63, 3, 9)])
+def test_per_symbol_lattice_count_matches_state_grid_loop(seed, N, xmax):
+    """One codebook per symbol: one lattice per (i, s', D) whose start position
+    n i + s' - xmax lies in [0, rho], counted by a plain loop."""
+    fr = synth.per_symbol_frame(np.random.default_rng(seed), 4, 3, N, 1, xmax, 0.1, 0.1, 0.02)
+    count = 0
+    for i in range(fr.N):
+        for s in range(2 * fr.xmax + 1):
+            if 0 <= fr.n * i + s - fr.xmax <= fr.rho:
+                count += fr.q
+    assert bench.lattices(fr) == count
+    one = synth.tiny_frame(seed, q=4, n=3, N=N, xmax=xmax)
+    assert bench.lattices(one) == (one.rho + 1) * one.q
