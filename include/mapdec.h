@@ -359,7 +359,7 @@ typedef struct {
                             (rho+1) * roundup4(q) * (n(I+1)+1) * 4 bytes per frame);
                             0 or -1: recompute them */
     int tensor_cores;    /* 0: the planner's rule (the forward producer on the tensor
-                            cores for frames whose tiles span at least 48 symbols,
+                            cores for frames whose tiles span at least 36 symbols,
                             the APP producer on the CUDA cores); 1: both producers on
                             the tensor cores wherever the class supports them (see
                             mapdec_batch_tc_frames); 2: FP32 CUDA-core producers */
@@ -383,7 +383,7 @@ int mapdec_batch_num_waves(mapdec_batch_t *b);
  * split into high and low parts, FP32 accumulation; an implementation choice,
  * not in the paper).  The planner picks the forward producer's for decode
  * batches, classes with q a multiple of 16 up to 64 and n >= 4 whose tiles fit
- * and span at least 48 symbols (MAPDEC_TC_MIN_S overrides the count); the
+ * and span at least 36 symbols (MAPDEC_TC_MIN_S overrides the count); the
  * other frames, and every frame of a MAPDEC_BATCH_GRAD batch, use the FP32
  * CUDA-core producers.  The environment variables, read when a batch is
  * created: MAPDEC_TC=0 keeps every producer on the CUDA cores, MAPDEC_TC=1

@@ -309,22 +309,32 @@ void plan_shape(FrameDev &f, const mapdec_frame_desc_t &d, bool grad, int forceP
 // (Pf <= 512 / q positions), at most 256 symbols from the 8-aligned first one
 // (the MMA's N), the shared memory within the two-CTA budget: frames with wide
 // drift limits get short tiles (their priors block is large), narrow ones long
-// tiles.  Sets Pf, Sf, Tf; false if no tile fits (the CUDA-core producer is
-// used).
+// tiles; among those, the tile that keeps the most threads busy in its rounds
+// of lattices.  Sets Pf, Sf, Tf; false if no tile fits (the CUDA-core producer
+// is used).
 bool plan_fwd_tc(FrameDev &f) {
     if (!fwd_tc_supported(f.q, f.n, f.I)) return false;
+    // among the tiles that fit, the most positions per round of lattices
+    // (P / ceil(P q / 256): one lattice per thread and round), then the longest
+    int best = 0;
+    double best_score = 0.0;
     for (int P = std::max(1, 512 / f.q); P >= 1; --P) {
         FrameDev t = f;
         t.Pf = P;
         t.Sf = (int)std::min<long long>(((long long)P - 1 + 2LL * f.xmax) / f.n + 2, f.N);
         if (((t.Sf + 7 + 15) & ~15) > 256) continue;
         if (fwd_tc_smem_bytes(t) > kFwdSmemBudget) continue;
-        f.Pf = t.Pf;
-        f.Sf = t.Sf;
-        f.Tf = (int)((f.rho + 1 + P - 1) / P);
-        return true;
+        const double score = (double)P / (double)((P * f.q + kThreads - 1) / kThreads);
+        if (score > best_score) {
+            best_score = score;
+            best = P;
+        }
     }
-    return false;
+    if (best == 0) return false;
+    f.Pf = best;
+    f.Sf = (int)std::min<long long>(((long long)best - 1 + 2LL * f.xmax) / f.n + 2, f.N);
+    f.Tf = (int)((f.rho + 1 + best - 1) / best);
+    return true;
 }
 
 // APP-producer tiling of the tensor-core kernel (decode mode): one lattice per
@@ -402,7 +412,7 @@ double frame_cost(const FrameDev &f) {
 using ClassKey = std::tuple<int, int, int>;  // n, I, tensor-core bits (kTcFwd | kTcBwd)
 
 constexpr int kTcFwd = 1, kTcBwd = 2;  // ClassKey / FrameHost tensor-core bits
-constexpr int kTcMinSymbols = 48;      // default rule: tensor-core forward producer from this
+constexpr int kTcMinSymbols = 36;      // default rule: tensor-core forward producer from this
                                        // many symbols per tile
 constexpr int kPerSym = 4;             // ClassKey: per-symbol-codebook producers
 

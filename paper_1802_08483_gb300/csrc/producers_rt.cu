@@ -131,9 +131,9 @@ bool fwd_tc_supported(int q, int n, int I) {
 
 size_t fwd_tc_smem_bytes(const FrameDev &f) {
     const size_t MNp = ((size_t)f.MN + 7) & ~(size_t)7;
-    const size_t MT = ((size_t)f.Pf * MNp + 127) / 128;
+    const size_t NRa = std::max<size_t>(128, ((size_t)f.Pf * MNp + 7) & ~(size_t)7);
     const size_t NN = ((size_t)f.Sf + 7 + 15) & ~(size_t)15;  // from the 8-aligned first symbol
-    const size_t b = (MT * 128 + NN) * (size_t)f.q * 6;      // three bf16 pieces of both operands
+    const size_t b = (NRa + NN) * (size_t)f.q * 6;           // three bf16 pieces of both operands
     return b < kTcMinSmem ? kTcMinSmem : b;
 }
 

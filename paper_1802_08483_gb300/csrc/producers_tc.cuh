@@ -90,14 +90,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restri
     const int NNa = (ihi - ilo8 + 1 + 15) & ~15;
     const int NR = P * MNp;
     const int MT = (NR + 127) >> 7;
-    const int mg = MT * 16;  // 8-row groups of the R operand
+    // rows held in shared memory: NR rounded up to 8, at least one M-tile.  The
+    // last M-tile starts at NRa - 128 (overlapping the one before when NR is
+    // not a multiple of 128) and stores only the rows past the earlier tiles.
+    const int NRa = max(128, (NR + 7) & ~7);
+    const int mg = NRa >> 3;  // 8-row groups of the R operand
+    auto mt0 = [&](int t) { return min(t * 128, NRa - 128); };
     const int kc = q >> 3;
     const int nbuf = NNa <= 128 ? 2 : 1;
     const uint32_t pbytes = (uint32_t)(NNa >> 3) * 3u * (uint32_t)kc * 128u;
 
     extern __shared__ __align__(128) unsigned char tsm[];
-    unsigned char *R0 = tsm;  // piece k at R0 + k * MT 128 q 2
-    const size_t rpiece = (size_t)MT * 128 * q * 2;
+    unsigned char *R0 = tsm;  // piece k at R0 + k * NRa q 2
+    const size_t rpiece = (size_t)NRa * q * 2;
     unsigned char *Pb = R0 + 3 * rpiece;
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_bar[3];  // [0], [1]: MMA accumulators; [2]: priors copy
@@ -152,23 +157,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restri
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = tc::idesc_bf16(128, NNa) | (1u << 15);  // A MN-major
 
-    // MMAs of M-tile t into accumulator t % nbuf (one thread)
+    // MMAs of M-tile t into accumulator t % nbuf (one thread).  The operands of
+    // one MMA differ from the first one's only in their start addresses, which
+    // sit in the descriptors' low field (address / 16, below 2^14: no carry), so
+    // the descriptors are formed once and offset per MMA.
+    const uint64_t da0 = tc::smem_desc_mn(smem_u32(R0), (uint32_t)mg);
+    const uint64_t db0 = tc::smem_desc_kmajor(smem_u32(Pb), 3u * (uint32_t)kc);
+    const uint32_t a_piece = (uint32_t)(rpiece >> 4), a_kstep = (uint32_t)mg * 16u;  // 16-byte units
+    const uint32_t b_piece = (uint32_t)kc * 8u;
     auto issue = [&](int t) {
         const uint32_t d = tmem + (uint32_t)((t % nbuf) * 128);
-        const uint32_t rb = smem_u32(R0) + (uint32_t)t * 16u * 128u;
-        const uint32_t pbs = smem_u32(Pb);
-        const int pa[6] = {0, 0, 1, 0, 1, 2}, pp[6] = {0, 1, 0, 2, 1, 0};
-        for (int k0 = 0; k0 < q; k0 += 16) {
-#pragma unroll
-            for (int pr = 0; pr < 6; ++pr) {
-                const uint32_t a = rb + (uint32_t)pa[pr] * (uint32_t)rpiece +
-                                   (uint32_t)(k0 >> 3) * (uint32_t)mg * 128u;
-                const uint32_t bsm = pbs + (uint32_t)pp[pr] * (uint32_t)kc * 128u +
-                                     (uint32_t)(k0 >> 3) * 128u;
-                const uint64_t da = tc::smem_desc_mn(a, (uint32_t)mg);
-                const uint64_t db = tc::smem_desc_kmajor(bsm, 3u * (uint32_t)kc);
-                tc::mma_bf16(d, da, db, idesc, (k0 > 0 || pr > 0) ? 1u : 0u);
-            }
+        const uint64_t da_t = da0 + (uint64_t)(mt0(t) >> 3) * 8u;  // 128 bytes per 8-row group
+        uint32_t ak = 0, bk = 0;
+        for (int k0 = 0; k0 < q; k0 += 16, ak += a_kstep, bk += 16u) {
+            const uint64_t da = da_t + ak, db = db0 + bk;
+            // pieces (A, B): (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+            tc::mma_bf16(d, da, db, idesc, k0 > 0 ? 1u : 0u);
+            tc::mma_bf16(d, da, db + b_piece, idesc, 1u);
+            tc::mma_bf16(d, da + a_piece, db, idesc, 1u);
+            tc::mma_bf16(d, da, db + 2u * b_piece, idesc, 1u);
+            tc::mma_bf16(d, da + a_piece, db + b_piece, idesc, 1u);
+            tc::mma_bf16(d, da + 2u * a_piece, db, idesc, 1u);
         }
         tc::commit(&s_bar[t % nbuf]);
     };
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restri
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        const int m = t * 128 + lg * 32 + lane;
+        const int m = mt0(t) + lg * 32 + lane;
         const int pl = m / MNp, j = m - pl * MNp;
         const long long p = p0 + pl;
         // this row's symbols: drift state s = p + xmax - n i inside [0, M), so
@@ -201,7 +210,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restri
         const long long pw = p + xmax;
         int clo = (int)max((long long)ilo, ceildiv(pw - M + 1, n)) - ilo8;
         int chi = (int)min((long long)ihi, floordiv(pw, n)) - ilo8;
-        if (!(pl < P && j < MN && p <= rho) || s_fail) chi = -1;  // nothing to store
+        // nothing to store (or stored by the M-tile before, which this one overlaps)
+        if (!(pl < P && j < MN && p <= rho) || m < t * 128 || s_fail) chi = -1;
         // W[i][s][j] = W + pw MNS + j + i (wblk - n MNS)
         float *wrow = f.W + (size_t)pw * f.MNS + j + (size_t)ilo8 * (f.wblk - (long long)n * f.MNS);
         const long long wstep = f.wblk - (long long)n * f.MNS;
@@ -420,18 +430,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tc(const FrameDev *__restri
             __syncthreads();
             if (tid == 0) {
                 tc::fence_after_sync();
-                const uint32_t ah = smem_u32(A0), al = ah + (uint32_t)apiece;
-                const uint32_t rh = smem_u32(R0), rl = rh + (uint32_t)rpiece;
+                // descriptors formed once, offset per K step (start address / 16 in
+                // their low field, below 2^14)
+                const uint64_t dah = tc::smem_desc(smem_u32(A0), kcA);
+                const uint64_t dal = dah + (uint64_t)(apiece >> 4);
+                const uint64_t drh = tc::smem_desc(smem_u32(R0), kcR) + (uint64_t)((c0 >> 3) * 8);
+                const uint64_t drl = drh + (uint64_t)(rpiece >> 4);
                 for (int k0 = 0; k0 < w; k0 += 16) {
-                    const uint32_t ao = (uint32_t)(k0 >> 3) * 128u;
-                    const uint32_t ro = (uint32_t)((c0 + k0) >> 3) * 128u;
-                    tc::mma_bf16(tmem, tc::smem_desc(ah + ao, kcA), tc::smem_desc(rh + ro, kcR),
-                                 idesc, issued ? 1u : 0u);
+                    const uint64_t o = (uint64_t)((k0 >> 3) * 8);  // 128 bytes per 8-column chunk
+                    tc::mma_bf16(tmem, dah + o, drh + o, idesc, issued ? 1u : 0u);
                     issued = true;
-                    tc::mma_bf16(tmem, tc::smem_desc(ah + ao, kcA), tc::smem_desc(rl + ro, kcR),
-                                 idesc, 1u);
-                    tc::mma_bf16(tmem, tc::smem_desc(al + ao, kcA), tc::smem_desc(rh + ro, kcR),
-                                 idesc, 1u);
+                    tc::mma_bf16(tmem, dah + o, drl + o, idesc, 1u);
+                    tc::mma_bf16(tmem, dal + o, drh + o, idesc, 1u);
                 }
                 tc::commit(&s_bar);
             }
