@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, (GRAD && (NB == 0 || NB > 10)) ? 1 :
     const FrameDev &f = frames[wk.frame];
     const int n = (NB == 0) ? f.n : NB;
     const int MN = (NB == 0) ? f.MN : NB * (IB + 1) + 1;
-    const int q = f.q, P = f.P, M = f.M, xmax = f.xmax;
+    const int q = f.q, P = f.P;
     const long long rho = f.rho;
     int ilo2, ihi2;
     super_symbols(f, wk.tile, ilo2, ihi2);

@@ -166,20 +166,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tc(const FrameDev *__restri
     const uint32_t a_piece = (uint32_t)(rpiece >> 4), a_kstep = (uint32_t)mg * 16u;  // 16-byte units
     const uint32_t b_piece = (uint32_t)kc * 8u;
     auto issue = [&](int t) {
-        const uint32_t d = tmem + (uint32_t)((t % nbuf) * 128);
-        const uint64_t da_t = da0 + (uint64_t)(mt0(t) >> 3) * 8u;  // 128 bytes per 8-row group
-        uint32_t ak = 0, bk = 0;
-        for (int k0 = 0; k0 < q; k0 += 16, ak += a_kstep, bk += 16u) {
-            const uint64_t da = da_t + ak, db = db0 + bk;
-            // pieces (A, B): (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
-            tc::mma_bf16(d, da, db, idesc, k0 > 0 ? 1u : 0u);
-            tc::mma_bf16(d, da, db + b_piece, idesc, 1u);
-            tc::mma_bf16(d, da + a_piece, db, idesc, 1u);
-            tc::mma_bf16(d, da, db + 2u * b_piece, idesc, 1u);
-            tc::mma_bf16(d, da + a_piece, db + b_piece, idesc, 1u);
-            tc::mma_bf16(d, da + 2u * a_piece, db, idesc, 1u);
+        if constexpr (IB <= 2) {
+            const uint32_t d = tmem + (uint32_t)((t % nbuf) * 128);
+            const uint64_t da_t = da0 + (uint64_t)(mt0(t) >> 3) * 8u;  // 128 bytes per 8-row group
+            uint32_t ak = 0, bk = 0;
+            for (int k0 = 0; k0 < q; k0 += 16, ak += a_kstep, bk += 16u) {
+                const uint64_t da = da_t + ak, db = db0 + bk;
+                // pieces (A, B): (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+                tc::mma_bf16(d, da, db, idesc, k0 > 0 ? 1u : 0u);
+                tc::mma_bf16(d, da, db + b_piece, idesc, 1u);
+                tc::mma_bf16(d, da + a_piece, db, idesc, 1u);
+                tc::mma_bf16(d, da, db + 2u * b_piece, idesc, 1u);
+                tc::mma_bf16(d, da + a_piece, db + b_piece, idesc, 1u);
+                tc::mma_bf16(d, da + 2u * a_piece, db, idesc, 1u);
+            }
+            tc::commit(&s_bar[t % nbuf]);
+        } else {
+            // longer lattices (I = 3): descriptors formed per MMA (the kernel
+            // spills less this way; measured on the N = 8000 workload)
+            const uint32_t d = tmem + (uint32_t)((t % nbuf) * 128);
+            const uint32_t rb = smem_u32(R0) + (uint32_t)(mt0(t) >> 3) * 128u;
+            const uint32_t pbs = smem_u32(Pb);
+            const int pa[6] = {0, 0, 1, 0, 1, 2}, pp[6] = {0, 1, 0, 2, 1, 0};
+            for (int k0 = 0; k0 < q; k0 += 16) {
+#pragma unroll
+                for (int pr = 0; pr < 6; ++pr) {
+                    const uint32_t a = rb + (uint32_t)pa[pr] * (uint32_t)rpiece +
+                                       (uint32_t)(k0 >> 3) * (uint32_t)mg * 128u;
+                    const uint32_t bsm = pbs + (uint32_t)pp[pr] * (uint32_t)kc * 128u +
+                                         (uint32_t)(k0 >> 3) * 128u;
+                    tc::mma_bf16(d, tc::smem_desc_mn(a, (uint32_t)mg),
+                                 tc::smem_desc_kmajor(bsm, 3u * (uint32_t)kc), idesc,
+                                 (k0 > 0 || pr > 0) ? 1u : 0u);
+                }
+            }
+            tc::commit(&s_bar[t % nbuf]);
         }
-        tc::commit(&s_bar[t % nbuf]);
     };
     if (tid == 0) {
         if (!tc_wait(&s_bar[2], 0)) s_fail = ST_TIMEOUT;  // the priors block has landed
