@@ -665,7 +665,29 @@ __global__ void k_grad_reduce(const FrameDev *__restrict__ frames, int nframes) 
 }
 
 // ---------------------------------------------------------------------------
+// Copies between pinned host memory and device memory by the SMs: 16 bytes per
+// thread and step over a grid-stride loop, reading or writing the host side
+// through its device mapping (NVLink-C2C).  Both pointers 16-byte aligned; n16
+// 16-byte words.
+__global__ void k_copy16(uint4 *__restrict__ dst, const uint4 *__restrict__ src, size_t n16) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n16; k += stride)
+        dst[k] = src[k];
+}
+
+// ---------------------------------------------------------------------------
 // Launch wrappers (host).
+cudaError_t launch_copy16(void *dst, const void *src, size_t n16, int sms, cudaStream_t st) {
+    if (n16 == 0) return cudaSuccess;
+    const size_t per = 256;
+    size_t blocks = (n16 + per - 1) / per;
+    const size_t cap = (size_t)(sms > 0 ? sms : 152) * 4;
+    if (blocks > cap) blocks = cap;
+    k_copy16<<<(unsigned)blocks, (unsigned)per, 0, st>>>(static_cast<uint4 *>(dst),
+                                                          static_cast<const uint4 *>(src), n16);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const FrameDev *frames, const uint8_t *const *rx_bytes,
                         uint32_t *const *rx_words, int nframes, long long max_words,
                         cudaStream_t st) {

@@ -67,15 +67,79 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of pinned (page-locked, mapped) host memory, or null for
+// pageable host memory and for device memory.
+void *mapped_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+int device_sms() {
+    static std::atomic<int> cache[64];  // 0 = not yet read on that device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+// Host <-> device copies of the batch's inputs and outputs.  Pinned host
+// memory is moved by the SMs through its device mapping: a copy engine's
+// first pass over a buffer that kernels have just written or read runs at a
+// small fraction of its rate (measured: 14 against 210 GB/s on the 0.8 GB
+// prior and APP buffers right after a decode), while the SM copy is not
+// affected.  Small copies (latency-bound either way), unaligned and pageable
+// host buffers go through the copy engine.
+constexpr size_t kSmCopyMin = 1 << 20;
+bool sm_copy(const void *a, const void *b, size_t bytes) {
+    return bytes >= kSmCopyMin && (((uintptr_t)a | (uintptr_t)b) & 15u) == 0;
+}
 void copy_in(void *dst_dev, const void *src, size_t bytes, cudaStream_t st) {
     if (bytes == 0 || src == dst_dev) return;  // already resident (caller passed the batch's own buffer)
-    CK(cudaMemcpyAsync(dst_dev, src, bytes,
-                       is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (is_device_ptr(src)) {
+        CK(cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyDeviceToDevice, st));
+        return;
+    }
+    void *m = mapped_host(src);
+    if (m && sm_copy(m, dst_dev, bytes)) {
+        // the tail (under 16 bytes) by the copy engine from the host address
+        const size_t head = bytes / 16 * 16;
+        CK(launch_copy16(dst_dev, m, bytes / 16, device_sms(), st));
+        if (head < bytes)
+            CK(cudaMemcpyAsync(static_cast<char *>(dst_dev) + head,
+                               static_cast<const char *>(src) + head, bytes - head,
+                               cudaMemcpyHostToDevice, st));
+        return;
+    }
+    CK(cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyHostToDevice, st));
 }
 void copy_out(void *dst, const void *src_dev, size_t bytes, cudaStream_t st) {
-    if (bytes == 0 || !dst) return;
-    CK(cudaMemcpyAsync(dst, src_dev, bytes,
-                       is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (bytes == 0 || !dst || dst == src_dev) return;
+    if (is_device_ptr(dst)) {
+        CK(cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDeviceToDevice, st));
+        return;
+    }
+    void *m = mapped_host(dst);
+    if (m && sm_copy(m, src_dev, bytes)) {
+        const size_t head = bytes / 16 * 16;
+        CK(launch_copy16(m, src_dev, bytes / 16, device_sms(), st));
+        if (head < bytes)
+            CK(cudaMemcpyAsync(static_cast<char *>(dst) + head,
+                               static_cast<const char *>(src_dev) + head, bytes - head,
+                               cudaMemcpyDeviceToHost, st));
+        return;
+    }
+    CK(cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDeviceToHost, st));
 }
 
 size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -74,6 +74,9 @@ constexpr size_t kTcMinSmem = 80 * 1024;  // caps the tensor-core producers at 2
 constexpr int kTcChunkCols = 80;          // A-operand columns per chunk of the APP producer
 size_t bwd_smem_bytes(const FrameDev &f, bool grad);
 
+// dst[k] = src[k] for n16 16-byte words (both 16-byte aligned device addresses,
+// either of them the device mapping of pinned host memory), by the SMs.
+cudaError_t launch_copy16(void *dst, const void *src, size_t n16, int sms, cudaStream_t st);
 cudaError_t launch_pack(const FrameDev *frames, const uint8_t *const *rx_bytes,
                         uint32_t *const *rx_words, int nframes, long long max_words,
                         cudaStream_t st);
