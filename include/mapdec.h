@@ -35,6 +35,10 @@
  *   - Arithmetic: FP32 for the lattice, gamma, alpha, beta and APPs; FP64 for
  *     the sum of log normalisers and for gradient reductions.
  *   - Every data pointer may be host or device memory (detected per call).
+ *     Pinned (page-locked) host buffers of at least 1 MiB whose address is a
+ *     multiple of 16 bytes are read or written by a copy kernel through their
+ *     device mapping; other host buffers by the copy engine (pageable memory
+ *     is staged by the driver and is much slower).
  *     The caller owns all buffers; a handle owns its device scratch.
  *     Work is issued on the handle's stream.  mapdec_decode,
  *     mapdec_decode_ext, mapdec_loglik_grad, mapdec_receiver_metric,
