@@ -543,6 +543,15 @@ def main():
         tuning = os.path.relpath(args.tuning, ROOT)
 
     if args.configs:
+        # the other workloads keep the table's producer parameters (per class)
+        # and use the planner's recursion setting: the table's is chosen for
+        # a batch whose recursions share the SMs with producers
+        if tuning:
+            table = json.load(open(args.tuning))
+            for e in table.get("entries", []):
+                for k in ("chain_budget_kb", "chain_stages", "chain_threads"):
+                    e["tune"][k] = 0
+            libtune.apply(table)
         props = torch.cuda.get_device_properties(local_rank)
         run_configs(props.multi_processor_count * 128 * 2 * 2070.0e6 / 1e12,
                     {int(c) for c in args.configs.split(",")})

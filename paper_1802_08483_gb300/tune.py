@@ -46,7 +46,8 @@ P_CANDIDATES = (0, 1, 2, 4, 8, 16, 32)
 NSUB_CANDIDATES = (0, 2, 4, 8, 16, 32)
 TC_CANDIDATES = (0, 2)  # planner's choice (tensor cores where supported), CUDA cores
 # recursion settings: (shared-memory budget KB, stages, threads); 0 = planner's
-CHAIN_CANDIDATES = ((0, 0, 0), (72, 2, 0), (150, 2, 0), (100, 3, 0), (0, 0, 128), (0, 0, 512))
+CHAIN_CANDIDATES = ((0, 0, 0), (72, 2, 0), (150, 2, 0), (100, 3, 0), (0, 0, 128), (0, 0, 512),
+                    (48, 2, 128), (52, 2, 128))
 
 
 def class_of(fr) -> Tuple[int, int, int]:

@@ -51,8 +51,7 @@ def _pool_decode(items, procs):
         return pool.map(_oracle_decode, items, chunksize=1)
 
 
-def test_mixed_4096_full_batch():
-    frames = [synth.config_frame(3, f) for f in range(4096)]
+def _decode_mixed(frames):
     b = mapdec.Batch(frames, flags=mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_TIMING)
     rx, pr = b.concat_inputs()
     st, app, ll = b.decode(rx, pr)
@@ -64,6 +63,25 @@ def test_mixed_4096_full_batch():
     for k, fr in enumerate(frames):
         s = apps[k].sum(axis=1)
         assert np.all(np.abs(s - 1) < 1e-4), k
+    b.close()
+    return apps, ll
+
+
+def test_mixed_4096_full_batch():
+    """The whole workload in one batch with the planner's launch parameters
+    and with the committed tuning table (the benchmark's: tuned tiles and the
+    128-thread, 52 KB recursions), both against the FP64 oracle."""
+    from paper_1802_08483_gb300 import tune
+    frames = [synth.config_frame(3, f) for f in range(4096)]
+    runs = [("planner", _decode_mixed(frames))]
+    import os
+    table = os.path.join(os.path.dirname(__file__), "..", "paper_1802_08483_gb300", "tuning",
+                         "gb300_mixed4096.json")
+    tune.load(table)
+    try:
+        runs.append(("tuned", _decode_mixed(frames)))
+    finally:
+        mapdec.mapdec_tune_clear()
     # sample: per (q, n) class the two cheapest frames for the oracle, plus a few
     # from each end of the batch, so every wave and every class is covered
     cost = {k: fr.N * (2 * fr.xmax + 1) * fr.q * (fr.n * 3 + 1) for k, fr in enumerate(frames)}
@@ -76,27 +94,27 @@ def test_mixed_4096_full_batch():
     sample.update(tail + head)
     sample = sorted(sample)
     refs = _pool_decode([(3, k) for k in sample], 8)
-    worst = 0.0
-    for k, (app_ref, ll_ref) in zip(sample, refs):
-        rel, ab = check_app(apps[k], app_ref, what=f"frame {k}")
-        check_ll(ll[k], ll_ref, what=f"frame {k}")
-        worst = max(worst, rel)
-    print(f"mixed-4096: {len(sample)} frames checked, worst APP rel {worst:.2e}")
+    for name, (apps, ll) in runs:
+        worst = 0.0
+        for k, (app_ref, ll_ref) in zip(sample, refs):
+            rel, ab = check_app(apps[k], app_ref, what=f"{name}: frame {k}")
+            check_ll(ll[k], ll_ref, what=f"{name}: frame {k}")
+            worst = max(worst, rel)
+        print(f"mixed-4096 ({name}): {len(sample)} frames checked, worst APP rel {worst:.2e}")
     # the costliest frames of every (q, n) class (N near 4000, the widest drift
     # limits), which dominate the timed step, against committed FP64 oracle
     # references (tests/golden/make_mixed_golden.py: every 16th symbol's APPs
     # and log P; kappa = 1.5 for two of them)
-    import os
     gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "mixed4096_heavy.npz"))
     stride = int(gold["stride"])
     assert {(frames[int(k)].q, frames[int(k)].n) for k in gold["frames"]} == set(synth.QN_CHOICES)
-    for k in [int(x) for x in gold["frames"]]:
-        rel, ab = check_app(apps[k][::stride], gold[f"app{k}"], what=f"heavy frame {k}")
-        llr = check_ll(ll[k], float(gold[f"ll{k}"]), what=f"heavy frame {k}")
-        fr = frames[k]
-        print(f"mixed-4096 heavy frame {k} (q={fr.q} n={fr.n} N={fr.N} xmax={fr.xmax}): "
-              f"APP rel {rel:.2e} abs {ab:.2e}, log P rel {llr:.2e}")
-    b.close()
+    for name, (apps, ll) in runs:
+        for k in [int(x) for x in gold["frames"]]:
+            rel, ab = check_app(apps[k][::stride], gold[f"app{k}"], what=f"{name}: heavy frame {k}")
+            llr = check_ll(ll[k], float(gold[f"ll{k}"]), what=f"{name}: heavy frame {k}")
+            fr = frames[k]
+            print(f"mixed-4096 ({name}) heavy frame {k} (q={fr.q} n={fr.n} N={fr.N} "
+                  f"xmax={fr.xmax}): APP rel {rel:.2e} abs {ab:.2e}, log P rel {llr:.2e}")
 
 
 def test_grad_256_fd_on_first_frames():
