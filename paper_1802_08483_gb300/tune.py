@@ -21,9 +21,11 @@ The producer parameters are searched per class, coordinate by coordinate
 (tile size, super-tile depth, store-or-recompute), each candidate scored by
 the producer phases' device time (events the library records at phase
 boundaries) on a sample of the class's frames.  The recursion parameters
-trade per-chain latency against chains resident per SM, which only the full
-mix of frames shows, so they are chosen once for all classes by the wall
-time of a large sample of the whole workload.  Choices go to the
+trade per-chain latency against chains resident per SM beside the producers,
+which only the full mix of frames shows, so they are chosen once for all
+classes by the wall time of a large sample of the whole workload (the
+--chain-sample frames; 0 = all of them, which is what the co-residence of
+recursions and producers needs to show in full).  Choices go to the
 process-wide tuning table (mapdec_tune_set) and can be saved as JSON and
 loaded again.  Only measurement and bookkeeping live here: every timed run
 executes the library's kernels.
@@ -62,8 +64,9 @@ def classes(frames) -> Dict[Tuple[int, int, int], List[int]]:
 
 
 def sample_indices(idx: List[int], count: int) -> List[int]:
-    """`count` indices spread evenly over idx (all of them if there are fewer)."""
-    if len(idx) <= count:
+    """`count` indices spread evenly over idx (all of them if there are fewer,
+    or if count <= 0)."""
+    if count <= 0 or len(idx) <= count:
         return list(idx)
     pos = np.linspace(0, len(idx) - 1, count).round().astype(int)
     return [idx[p] for p in pos]
@@ -152,7 +155,7 @@ def tune_chains(entries, frames, reps: int = 2, log=None,
             "wall_ms": best[0], "sample_frames": len(frames)}
 
 
-def tune(frames, sample: int = 48, chain_sample: int = 1024, reps: int = 3, log=None,
+def tune(frames, sample: int = 48, chain_sample: int = 0, reps: int = 3, log=None,
          chain_candidates: Iterable[Tuple[int, int]] = CHAIN_CANDIDATES, **kw) -> dict:
     """Tune every (q, n, I) class of `frames`; returns the JSON-ready table."""
     mapdec.load()
@@ -194,8 +197,8 @@ def main(argv: Optional[List[str]] = None) -> int:
     ap.add_argument("--config", type=int, default=3, help="workload: synthetic config 1..5")
     ap.add_argument("--frames", type=int, default=0, help="frames of the workload (0 = all)")
     ap.add_argument("--sample", type=int, default=48, help="frames timed per class")
-    ap.add_argument("--chain-sample", type=int, default=1024,
-                    help="frames of the whole workload timed for the recursion setting")
+    ap.add_argument("--chain-sample", type=int, default=0,
+                    help="frames of the whole workload timed for the recursion setting (0 = all)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
