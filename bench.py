@@ -56,6 +56,16 @@ def lattice_cells(n, I):
     return (I + 1) * n * (n + 1) // 2 + n
 
 
+def producer_settings(table: dict) -> dict:
+    """A tuning table with its recursion setting reset to the planner's (the
+    per-class producer parameters kept)."""
+    out = json.loads(json.dumps(table))
+    for e in out.get("entries", []):
+        for k in ("chain_budget_kb", "chain_stages", "chain_threads"):
+            e["tune"][k] = 0
+    return out
+
+
 def lattices(fr) -> int:
     """Receiver-metric lattices a frame needs: one per (rx start p, codeword D)
     with one codebook; with one codebook per symbol the metric also depends on
@@ -547,11 +557,7 @@ def main():
         # and use the planner's recursion setting: the table's is chosen for
         # a batch whose recursions share the SMs with producers
         if tuning:
-            table = json.load(open(args.tuning))
-            for e in table.get("entries", []):
-                for k in ("chain_budget_kb", "chain_stages", "chain_threads"):
-                    e["tune"][k] = 0
-            libtune.apply(table)
+            libtune.apply(producer_settings(json.load(open(args.tuning))))
         props = torch.cuda.get_device_properties(local_rank)
         run_configs(props.multi_processor_count * 128 * 2 * 2070.0e6 / 1e12,
                     {int(c) for c in args.configs.split(",")})

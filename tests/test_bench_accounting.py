@@ -100,3 +100,18 @@ def test_per_symbol_lattice_count_matches_state_grid_loop(seed, N, xmax):
     assert bench.lattices(fr) == count
     one = synth.tiny_frame(seed, q=4, n=3, N=N, xmax=xmax)
     assert bench.lattices(one) == (one.rho + 1) * one.q
+
+
+def test_producer_settings_keep_tiles_and_reset_recursions():
+    import json
+    import os
+    table = json.load(open(os.path.join(os.path.dirname(__file__), "..", "paper_1802_08483_gb300",
+                                        "tuning", "gb300_mixed4096.json")))
+    out = bench.producer_settings(table)
+    for a, b in zip(table["entries"], out["entries"]):
+        assert (a["q"], a["n"], a["I"]) == (b["q"], b["n"], b["I"])
+        for k in ("P", "nsub", "store_metric"):
+            assert b["tune"][k] == a["tune"][k]
+        assert b["tune"]["chain_budget_kb"] == b["tune"]["chain_stages"] == 0
+        assert b["tune"]["chain_threads"] == 0
+    assert table["entries"][0]["tune"]["chain_threads"] == 128  # the input is not modified
