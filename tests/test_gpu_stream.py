@@ -113,3 +113,36 @@ def test_stream_single_handle_priors_set_and_cleared():
     with pytest.raises(mapdec.MapDecError):
         dec.set_drift_priors(np.zeros(2 * fr.xmax + 1, np.float32), None)
     dec.close()
+
+
+def _per_symbol_stream_frame(seed, q, n, N, I, xmax, p, pre, post, sd):
+    """A frame with one codebook per symbol, cut from a stream (both widenings
+    at once)."""
+    rng = np.random.default_rng(seed)
+    fr = synth.per_symbol_frame(rng, q, n, N, I, max(1, xmax - pre - post), p, p, 0.005)
+    body = fr.rx
+    fr.rx = np.concatenate([rng.integers(0, 2, pre), body,
+                            rng.integers(0, 2, post)]).astype(np.uint8)
+    tau = n * N
+    fr.xmax = xmax
+    fr.drift_start = synth._gauss_window(xmax, pre, sd, 0, xmax)
+    fr.drift_end = synth._gauss_window(xmax, pre + body.size - tau, sd, -xmax, fr.rx.size - tau)
+    return fr
+
+
+def test_per_symbol_codebooks_with_boundary_priors_against_oracle():
+    frames = [_per_symbol_stream_frame(861, 16, 10, 30, 2, 30, 0.03, 4, 6, 2.0),
+              _per_symbol_stream_frame(862, 5, 5, 50, 1, 20, 0.04, 3, 2, 1.5),
+              _per_symbol_stream_frame(863, 64, 12, 12, 2, 40, 0.05, 7, 5, 3.0)]
+    b = mapdec.Batch(frames, flags=mapdec.MAPDEC_BATCH_GRAPH | mapdec.MAPDEC_BATCH_EXTRINSIC)
+    rx, pr = b.concat_inputs()
+    st, app, ext, ll = b.decode_ext(rx, pr)
+    assert st == 0, mapdec.mapdec_strerror(st)
+    apps, exts = b.split(app), b.split(ext)
+    for k, fr in enumerate(frames):
+        app_ref, ext_ref, ll_ref = _ref(fr)
+        what = f"per-symbol stream frame {k} (q={fr.q})"
+        check_app(apps[k], app_ref, what=what)
+        check_app(exts[k], ext_ref, what=what + " extrinsic")
+        check_ll(ll[k], ll_ref, what=what)
+    b.close()
