@@ -66,3 +66,12 @@ def test_classes_and_samples():
     s = tune.sample_indices(idx, 7)
     assert len(s) == 7 and s[0] == 0 and s[-1] == 99 and s == sorted(set(s))
     assert tune.sample_indices(idx[:5], 7) == idx[:5]
+
+
+def test_sample_indices_spread_and_all():
+    from paper_1802_08483_gb300 import tune
+    idx = list(range(100, 110))
+    assert tune.sample_indices(idx, 0) == idx          # 0: every frame
+    assert tune.sample_indices(idx, 20) == idx         # fewer frames than asked: all
+    s = tune.sample_indices(idx, 3)
+    assert s[0] == 100 and s[-1] == 109 and len(s) == 3
